@@ -1,0 +1,202 @@
+/*
+ * yateto_gb300 — C ABI of a GB300 (sm_103a) library for the element kernels of
+ * tetrahedral ADER-DG (Uphoff & Bader, "Yet Another Tensor Toolbox for discontinuous
+ * Galerkin methods and other applications", arXiv 1903.11521).
+ *
+ * Two layers:
+ *   1. Planner + batched executor for small tensor contractions written in Einstein
+ *      notation (Sec. 4): yt_plan_create / yt_plan_stats_get / yt_plan_eqspp /
+ *      yt_execute_batched / yt_plan_destroy.
+ *   2. A fused solver for one elastic ADER-DG step (Sec. 5.1, Eqs. seissol:derivative,
+ *      seissol:timeint, seissol:correction_local, seissol:correction_neigh):
+ *      yt_solver_create / yt_solver_set_dofs / yt_solver_get / yt_step /
+ *      yt_step_local / yt_step_neighbour / yt_solver_destroy.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a yt_status; no exception or abort crosses the ABI.  After an
+ *     error, yt_last_error() returns a message for the calling thread.
+ *   - Device work is enqueued asynchronously on the given stream (0 = legacy default
+ *     stream); nothing synchronises unless stated.  A pointer marked "host" must be host
+ *     memory, "device" must be device memory of the current device.
+ *   - Tensors are column-major (first index fastest, Sec. 4.4, dense layout).
+ *   - Plans and solvers are owned by the library and freed by their destroy call.
+ *     Caller-provided buffers stay owned by the caller.
+ *   - A plan is immutable after creation and may be used from several threads; a solver
+ *     must not be stepped concurrently from several threads.
+ * There is no CPU fallback: without a CUDA device, calls that launch kernels return
+ * YT_ERR_CUDA.
+ */
+#ifndef YATETO_GB300_H
+#define YATETO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* yt_stream;   /* same type as cudaStream_t */
+
+typedef enum yt_status {
+  YT_OK = 0,
+  YT_ERR_INVALID = 1,      /* null pointer, out-of-range argument */
+  YT_ERR_PARSE = 2,        /* malformed Einstein expression */
+  YT_ERR_SHAPE = 3,        /* inconsistent index sizes / tensor dimensions */
+  YT_ERR_UNSUPPORTED = 4,  /* valid request that this build has no kernel for */
+  YT_ERR_OOM = 5,          /* device or host allocation failed */
+  YT_ERR_CUDA = 6,         /* a CUDA runtime call failed (incl. no device) */
+  YT_ERR_TIMEOUT = 7       /* a bounded device-side wait ran out */
+} yt_status;
+
+typedef enum yt_precision {
+  YT_F64 = 0,              /* all arithmetic in binary64 */
+  YT_F32 = 1,              /* bulk contractions in binary32, setup in binary64 */
+  YT_BF16X3_F32ACC = 2     /* reserved: split-bf16 tensor-core contractions */
+} yt_precision;
+
+typedef enum yt_memory { YT_MEM_HOST = 0, YT_MEM_DEVICE = 1 } yt_memory;
+
+typedef enum yt_field {
+  YT_FIELD_DOFS = 0,             /* Q, the degrees of freedom */
+  YT_FIELD_TIME_INTEGRAL = 1     /* I, the time-integrated DOFs of the last step */
+} yt_field;
+
+/* ------------------------------------------------------------------ diagnostics */
+const char* yt_status_string(yt_status s);
+/* Message of the last failing call on this thread ("" if none).  Valid until the next
+ * failing call on the same thread. */
+const char* yt_last_error(void);
+/* Library version string, e.g. "yateto_gb300 0.1 sm_103a". */
+const char* yt_version(void);
+
+/* ===================================================================== planner
+ *
+ * yt_plan_create parses an assignment in the DSL of Sec. 4.1
+ *     "Q[kp] += Kh[kl] * I[lq] * As[pq]"
+ *     "C[ij] = 2.0 * A[lj] * B[ikl] * w[k]"
+ *     "Q[kp] += Kx[kl] * I[lq] * Ax[pq] + Ky[kl] * I[lq] * Ay[pq]"
+ * LHS "=" or "+="; the RHS is a sum of terms, each an optional numeric scalar followed by
+ * a product of indexed tensors.  Index letters [a-zA-Z]; each tensor's index string must
+ * have one letter per dimension and no repeated letter (Sec. 4.2.1: the trace T_ii is not
+ * an Einstein product here).  Every letter of a term that is not on the LHS is summed.
+ * For every term the planner computes the equivalent sparsity patterns (Eq. compeqspp),
+ * the operation-minimal binary tree under the sparse cost of Sec. 4.3, the index
+ * permutations of the temporaries by the dynamic program of Sec. 4.5 (Eqs. permopt,
+ * permcost, subproblem) with the Loop-over-GEMM cost (s, l+r, -f), and the non-zero flop
+ * count.
+ */
+typedef struct yt_tensor_desc {
+  const char* name;         /* as used in the expression */
+  int32_t ndim;             /* 0..8 */
+  const int32_t* shape;     /* host, ndim entries */
+  const uint8_t* pattern;   /* host, column-major boolean non-zero pattern of prod(shape)
+                               bytes; NULL = dense */
+  const double* values;     /* host, column-major values of a global constant (uploaded
+                               and owned by the plan); NULL = per-element tensor */
+} yt_tensor_desc;
+
+typedef struct yt_plan_stats {
+  double nz_flops;           /* non-zero flops per element (Sec. 4.9) */
+  double hw_flops;           /* flops the executor performs per element */
+  double naive_flops;        /* cost of the unreduced n-ary product per element */
+  int64_t bytes_per_element; /* per-element tensor bytes read + written */
+  int32_t n_ops;             /* binary operations after strength reduction */
+  int32_t n_terms;
+  char order[1024];          /* parenthesised contraction order, e.g.
+                                "((B*w)_k*A)_l" ; temporaries' index orders appended */
+} yt_plan_stats;
+
+struct yt_plan;
+
+yt_status yt_plan_create(const char* expr, const yt_tensor_desc* tensors,
+                         int32_t n_tensors, yt_precision precision,
+                         struct yt_plan** out_plan);
+yt_status yt_plan_stats_get(const struct yt_plan* plan, yt_plan_stats* out);
+/* Equivalent sparsity pattern (Eq. compeqspp) of tensor `tensor_index` (position in the
+ * descriptor array) within term `term`; writes prod(shape) bytes (host, column-major). */
+yt_status yt_plan_eqspp(const struct yt_plan* plan, int32_t term, int32_t tensor_index,
+                        uint8_t* pattern_out);
+/* Runs the plan for n_elements elements.  element_tensors[i] is the device pointer of
+ * descriptor i if that descriptor is per-element (values == NULL), ignored otherwise.
+ * Per-element tensors are stored element after element, each dense column-major in the
+ * plan's precision (double for YT_F64, float for YT_F32).  The LHS tensor is read only
+ * for "+=".  Scratch for temporaries is allocated by the plan on first use. */
+yt_status yt_execute_batched(const struct yt_plan* plan, void* const* element_tensors,
+                             int64_t n_elements, yt_stream stream);
+void yt_plan_destroy(struct yt_plan* plan);
+
+/* ===================================================================== solver
+ *
+ * Elastic ADER-DG on tetrahedra (Sec. 5.1).  Quantities q = (sxx, syy, szz, sxy, syz,
+ * sxz, u, v, w); polynomial degree N = order - 1; B = C(N+3,3) Dubiner basis functions
+ * (degree-major, then lexicographic in (p, q) of phi_pqr).
+ *
+ * Per step (all on the device):
+ *   D^0 = Q,  D^{d+1} = sum_x Ktilde^x D^d Astar^x^T                (CK derivatives)
+ *   I = sum_{d=0}^{N} dt^{d+1}/(d+1)! D^d                          (time integral)
+ *   Q += sum_x Khat^x I Astar^x^T + sum_s Rhat^s R^sT I Aloc_s^T     (volume + local flux)
+ *   Q += sum_s Rhat^s f^h R^jT I_nb Anb_s^T,  (nb, j, h) = neighbour, its face, orientation
+ * with Khat^x = M^-1 K^x, Ktilde^x = -M^-1 K^xT, K^x_kl = int dphi_k/dxi_x phi_l,
+ * Astar^x = sum_j (dxi_x/dx_j) A^j and upwind flux solvers
+ * Aloc_s = -(2|S_s|/|J|)(A_n + |A_n|)/2, Anb_s = -(2|S_s|/|J|)(A_n - |A_n|)/2.
+ */
+typedef struct yt_mesh_desc {
+  int64_t n_elements;
+  const double* material;    /* host, E x 3: rho, lambda, mu per element */
+  const double* jacobian;    /* host, E x 9: dx/dxi of the affine map, column-major 3x3
+                                (column c = physical edge vector x_c - x_0) */
+  const int32_t* neighbours; /* host, E x 4: element behind face s (0..E-1), or NULL for
+                                a local-only solver (yt_step_neighbour then fails) */
+  const int8_t* faces;       /* host, E x 4: the neighbour's face index j (0..3) */
+  const int8_t* orient;      /* host, E x 4: orientation h (0..2) */
+} yt_mesh_desc;
+
+typedef struct yt_scheme_desc {
+  int32_t order;             /* convergence order O = N + 1; this build: 2..6 */
+  double dt;                 /* time step */
+  yt_precision precision;    /* YT_F64 or YT_F32 */
+  int32_t flags;             /* reserved, must be 0 */
+} yt_scheme_desc;
+
+struct yt_solver;
+
+/* Builds the reference matrices, uploads material, geometry and connectivity and runs
+ * the per-element setup kernel (star matrices, flux solvers) on `stream`.  Device memory
+ * is allocated here; DOFs start at zero. */
+yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
+                           yt_stream stream, struct yt_solver** out_solver);
+/* Copies Q in: `dofs` holds E x 9 x B values in the canonical element layout
+ * [element][quantity][basis] (basis index fastest, column-major B x 9 per element), as
+ * double, in host or device memory (`where`).  Asynchronous on `stream`; host memory must
+ * stay valid until the stream reaches this point (use pinned memory to overlap). */
+yt_status yt_solver_set_dofs(struct yt_solver* solver, const double* dofs, yt_memory where,
+                             yt_stream stream);
+/* Copies a field out in the canonical layout (as above), as double. */
+yt_status yt_solver_get(struct yt_solver* solver, yt_field field, double* out,
+                        yt_memory where, yt_stream stream);
+/* One full step: the local kernel (derivatives, time integral, volume, local flux),
+ * then the neighbour kernel. */
+yt_status yt_step(struct yt_solver* solver, yt_stream stream);
+/* The two halves of yt_step, for partial updates and timing. */
+yt_status yt_step_local(struct yt_solver* solver, yt_stream stream);
+yt_status yt_step_neighbour(struct yt_solver* solver, yt_stream stream);
+/* Non-zero flops per element of the local / neighbour kernels and their device bytes
+ * per element (algorithmic: each stream read or written once). */
+yt_status yt_solver_stats(const struct yt_solver* solver, double* local_flops,
+                          double* neighbour_flops, double* local_bytes,
+                          double* neighbour_bytes);
+/* Reference matrix `name` ("M", "Khat", "Ktilde", "R", "Rhat", "f") of this solver's
+ * order as double, column-major, stacked over its first index (3, 4 or 3 matrices);
+ * `count` receives the number of doubles; pass out == NULL to query the size. */
+yt_status yt_solver_reference_matrix(const struct yt_solver* solver, const char* name,
+                                     double* out, int64_t* count);
+void yt_solver_destroy(struct yt_solver* solver);
+
+/* Host-only: reference matrices for an order without creating a solver (same meaning as
+ * yt_solver_reference_matrix).  Runs no device code. */
+yt_status yt_reference_matrix(int32_t order, const char* name, double* out, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YATETO_GB300_H */

@@ -1,0 +1,514 @@
+// Elastic ADER-DG solver: device buffers, setup kernel, layout conversion and the C ABI
+// entry points yt_solver_* / yt_step* (Sec. 5.1 of the paper).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ader_kernels.cuh"
+#include "common.h"
+#include "tables.h"
+
+using namespace yt;
+
+namespace {
+
+// Elastic Jacobians A^j (j = x, y, z) of the velocity-stress system
+// q = (sxx, syy, szz, sxy, syz, sxz, u, v, w): eight entries each.
+// kind 0: -(lambda + 2 mu), 1: -lambda, 2: -mu, 3: -1/rho.
+struct JacEntry { int8_t p, q, kind; };
+__constant__ JacEntry c_jac[3][8] = {
+    {{0, 6, 0}, {1, 6, 1}, {2, 6, 1}, {3, 7, 2}, {5, 8, 2}, {6, 0, 3}, {7, 3, 3}, {8, 5, 3}},
+    {{0, 7, 1}, {1, 7, 0}, {2, 7, 1}, {3, 6, 2}, {4, 8, 2}, {6, 3, 3}, {7, 1, 3}, {8, 4, 3}},
+    {{0, 8, 1}, {1, 8, 1}, {2, 8, 0}, {4, 7, 2}, {5, 6, 2}, {6, 5, 3}, {7, 4, 3}, {8, 2, 3}}};
+// Star slots grouped by row (union of the three patterns): row p owns slots
+// [start[p], start[p+1]) with columns col[slot].
+const StarPattern kStar = {{0, 3, 6, 9, 11, 13, 15, 18, 21, 24},
+                           {6, 7, 8, 6, 7, 8, 6, 7, 8, 6, 7, 7, 8, 6, 8, 0, 3, 5, 1, 3, 4, 2, 4, 5}};
+__constant__ StarPattern c_star;
+
+const int kFaceVerts[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
+__constant__ int c_face_verts[4][3];
+
+__device__ void mat9_mul(const double* a, const double* b, double* c) {
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 9; ++k) s = fma(a[i * 9 + k], b[k * 9 + j], s);
+      c[i * 9 + j] = s;
+    }
+}
+
+// Setup (not part of a step): star matrices Astar^x = sum_j (dxi_x/dx_j) A^j and upwind
+// flux solvers -(2|S|/|J|)(A_n +- |A_n|)/2.  |A_n| = alpha A_n^2 + beta A_n^4 is the even
+// polynomial interpolating |lambda| on the spectrum {0, +-c_s, +-c_p} of the
+// diagonalisable A_n: alpha = (cp^2 + cp cs + cs^2) / (cp cs (cp + cs)),
+// beta = -1 / (cp cs (cp + cs)).  One thread per element.
+__global__ void k_setup(const double* __restrict__ material, const double* __restrict__ jac,
+                        int64_t E, int64_t Epad, double* __restrict__ star,
+                        double* __restrict__ floc, double* __restrict__ fnb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Epad) return;
+  const int64_t tile = e / kTile;
+  const int lane = (int)(e % kTile);
+  if (e >= E) {
+    for (int i = 0; i < 3 * kStarSlots; ++i) star[(tile * 3 * kStarSlots + i) * kTile + lane] = 0.0;
+    for (int i = 0; i < 4 * 81; ++i) {
+      floc[(tile * 4 * 81 + i) * kTile + lane] = 0.0;
+      fnb[(tile * 4 * 81 + i) * kTile + lane] = 0.0;
+    }
+    return;
+  }
+  const double rho = material[e * 3 + 0], lam = material[e * 3 + 1], mu = material[e * 3 + 2];
+  double J[9];
+  for (int i = 0; i < 9; ++i) J[i] = jac[e * 9 + i];       // J[i + 3c] = dx_i / dxi_c
+  auto Jm = [&](int i, int c) { return J[i + 3 * c]; };
+  const double det = Jm(0, 0) * (Jm(1, 1) * Jm(2, 2) - Jm(1, 2) * Jm(2, 1)) -
+                     Jm(0, 1) * (Jm(1, 0) * Jm(2, 2) - Jm(1, 2) * Jm(2, 0)) +
+                     Jm(0, 2) * (Jm(1, 0) * Jm(2, 1) - Jm(1, 1) * Jm(2, 0));
+  // G[d][j] = dxi_d / dx_j = (J^-1)_{dj} via the adjugate
+  double G[3][3];
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < 3; ++j) {
+      const int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (d + 1) % 3, c1 = (d + 2) % 3;
+      G[d][j] = (Jm(r0, c0) * Jm(r1, c1) - Jm(r0, c1) * Jm(r1, c0)) / det;
+    }
+  const double val[4] = {-(lam + 2.0 * mu), -lam, -mu, -1.0 / rho};
+  double A[3][81];
+  for (int j = 0; j < 3; ++j) {
+    for (int i = 0; i < 81; ++i) A[j][i] = 0.0;
+    for (int t = 0; t < 8; ++t) A[j][c_jac[j][t].p * 9 + c_jac[j][t].q] = val[c_jac[j][t].kind];
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int p = 0; p < kNq; ++p)
+      for (int s = c_star.start[p]; s < c_star.start[p + 1]; ++s) {
+        const int q = c_star.col[s];
+        double v = 0.0;
+        for (int j = 0; j < 3; ++j) v = fma(G[d][j], A[j][p * 9 + q], v);
+        star[((tile * 3 + d) * kStarSlots + s) * kTile + lane] = v;
+      }
+  const double cp = sqrt((lam + 2.0 * mu) / rho), cs = sqrt(mu / rho);
+  const double alpha = (cp * cp + cp * cs + cs * cs) / (cp * cs * (cp + cs));
+  const double beta = -1.0 / (cp * cs * (cp + cs));
+  const double V[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int s = 0; s < 4; ++s) {
+    double X[3][3];
+    for (int v = 0; v < 3; ++v)
+      for (int i = 0; i < 3; ++i) {
+        const double* r = V[c_face_verts[s][v]];
+        X[v][i] = Jm(i, 0) * r[0] + Jm(i, 1) * r[1] + Jm(i, 2) * r[2];
+      }
+    double u[3], t[3], c[3];
+    for (int i = 0; i < 3; ++i) { u[i] = X[1][i] - X[0][i]; t[i] = X[2][i] - X[0][i]; }
+    c[0] = u[1] * t[2] - u[2] * t[1];
+    c[1] = u[2] * t[0] - u[0] * t[2];
+    c[2] = u[0] * t[1] - u[1] * t[0];
+    const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double area = 0.5 * len;
+    double An[81], A2[81], A4[81];
+    for (int i = 0; i < 81; ++i) An[i] = (c[0] * A[0][i] + c[1] * A[1][i] + c[2] * A[2][i]) / len;
+    mat9_mul(An, An, A2);
+    mat9_mul(A2, A2, A4);
+    const double scale = -(2.0 * area / det) * 0.5;
+    for (int i = 0; i < 81; ++i) {
+      const double absA = alpha * A2[i] + beta * A4[i];
+      floc[((tile * 4 + s) * 81 + i) * kTile + lane] = scale * (An[i] + absA);
+      fnb[((tile * 4 + s) * 81 + i) * kTile + lane] = scale * (An[i] - absA);
+    }
+  }
+}
+
+// canonical [e][q][k] <-> element-blocked [tile][q][k][lane]
+__global__ void k_to_blocked(const double* __restrict__ in, double* __restrict__ out,
+                             int64_t E, int64_t Epad, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = Epad * kNq * B;
+  if (i >= total) return;
+  const int lane = (int)(i % kTile);
+  const int64_t rest = i / kTile;
+  const int k = (int)(rest % B);
+  const int q = (int)((rest / B) % kNq);
+  const int64_t tile = rest / ((int64_t)B * kNq);
+  const int64_t e = tile * kTile + lane;
+  out[i] = e < E ? in[(e * kNq + q) * B + k] : 0.0;
+}
+__global__ void k_from_blocked(const double* __restrict__ in, double* __restrict__ out,
+                               int64_t E, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * kNq * B) return;
+  const int k = (int)(i % B);
+  const int q = (int)((i / B) % kNq);
+  const int64_t e = i / ((int64_t)B * kNq);
+  out[i] = in[(((e / kTile) * kNq + q) * B + k) * kTile + (e % kTile)];
+}
+
+// --------------------------------------------------------------------- host helpers
+struct Csr {
+  std::vector<int> rp;
+  std::vector<uint16_t> col;
+  std::vector<double> val;
+  // Appends the CSR of a rows x cols view; `at(r, c)` gives the entry.  Returns the rp
+  // offset.  Flops of the lists are accumulated by the caller.
+  template <typename F>
+  int add(int rows, int cols, F at) {
+    const int off = static_cast<int>(rp.size());
+    for (int r = 0; r < rows; ++r) {
+      rp.push_back(static_cast<int>(col.size()));
+      for (int c = 0; c < cols; ++c) {
+        const double v = at(r, c);
+        if (v != 0.0) {
+          col.push_back(static_cast<uint16_t>(c));
+          val.push_back(v);
+        }
+      }
+    }
+    rp.push_back(static_cast<int>(col.size()));
+    return off;
+  }
+  int64_t row_nnz(int off, int r) const { return rp[off + r + 1] - rp[off + r]; }
+};
+
+template <typename T>
+T* dalloc(size_t n) {
+  T* p = nullptr;
+  cuda_check(cudaMalloc(&p, n * sizeof(T) + 16), "cudaMalloc");
+  return p;
+}
+
+}  // namespace
+
+struct yt_solver {
+  int N = 0, B = 0, BT = 0;
+  int64_t E = 0, Epad = 0, ntiles = 0;
+  yt_precision prec = YT_F64;
+  double dt = 0.0;
+  bool has_neighbours = false;
+  double *Q = nullptr, *I = nullptr, *Pface = nullptr, *star = nullptr, *floc = nullptr,
+         *fnb = nullptr, *staging = nullptr;
+  int* conn = nullptr;
+  int* d_rp = nullptr;
+  uint16_t* d_col = nullptr;
+  double* d_val = nullptr;
+  double* d_f = nullptr;
+  StepTables T{};
+  double flops_local = 0, flops_neigh = 0, bytes_local = 0, bytes_neigh = 0;
+  size_t smem_local = 0, smem_neigh = 0;
+  ~yt_solver() {
+    for (void* p : {(void*)Q, (void*)I, (void*)Pface, (void*)star, (void*)floc, (void*)fnb,
+                    (void*)staging, (void*)conn, (void*)d_rp, (void*)d_col, (void*)d_val,
+                    (void*)d_f})
+      if (p) cudaFree(p);
+  }
+};
+
+namespace {
+
+template <int N>
+void set_smem_attrs(yt_solver* s) {
+  using Dm = Dims<N>;
+  s->smem_local = sizeof(double) * (Dm::B + Dm::XR) * kNq * kTile;
+  s->smem_neigh = sizeof(double) * Dm::BT * kNq * kTile;
+  cuda_check(cudaFuncSetAttribute(k_local<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s->smem_local), "cudaFuncSetAttribute(k_local)");
+  cuda_check(cudaFuncSetAttribute(k_neigh<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s->smem_neigh), "cudaFuncSetAttribute(k_neigh)");
+}
+
+template <int N>
+void launch_local(yt_solver* s, cudaStream_t st) {
+  k_local<N><<<(unsigned)s->ntiles, kNq * kTile, s->smem_local, st>>>(
+      s->Q, s->Q, s->I, s->Pface, s->star, s->floc, s->T, kStar);
+}
+template <int N>
+void launch_neigh(yt_solver* s, cudaStream_t st) {
+  k_neigh<N><<<(unsigned)s->ntiles, kNq * kTile, s->smem_neigh, st>>>(s->Q, s->Pface, s->fnb,
+                                                                      s->conn, s->T);
+}
+
+void dispatch_smem(yt_solver* s) {
+  switch (s->N) {
+    case 1: set_smem_attrs<1>(s); break;
+    case 2: set_smem_attrs<2>(s); break;
+    case 3: set_smem_attrs<3>(s); break;
+    case 4: set_smem_attrs<4>(s); break;
+    case 5: set_smem_attrs<5>(s); break;
+    default: throw Error(YT_ERR_UNSUPPORTED, "FP64 solver supports orders 2..6");
+  }
+}
+void dispatch_local(yt_solver* s, cudaStream_t st) {
+  switch (s->N) {
+    case 1: launch_local<1>(s, st); break;
+    case 2: launch_local<2>(s, st); break;
+    case 3: launch_local<3>(s, st); break;
+    case 4: launch_local<4>(s, st); break;
+    case 5: launch_local<5>(s, st); break;
+    default: throw Error(YT_ERR_UNSUPPORTED, "order");
+  }
+  cuda_check(cudaGetLastError(), "k_local launch");
+}
+void dispatch_neigh(yt_solver* s, cudaStream_t st) {
+  switch (s->N) {
+    case 1: launch_neigh<1>(s, st); break;
+    case 2: launch_neigh<2>(s, st); break;
+    case 3: launch_neigh<3>(s, st); break;
+    case 4: launch_neigh<4>(s, st); break;
+    case 5: launch_neigh<5>(s, st); break;
+    default: throw Error(YT_ERR_UNSUPPORTED, "order");
+  }
+  cuda_check(cudaGetLastError(), "k_neigh launch");
+}
+
+// Builds the CSR tables of one order and the flop / byte counts of the two kernels.
+void build_tables(yt_solver* s) {
+  const RefMatrices& R = reference_matrices(s->N);
+  const int N = s->N, B = R.B, BT = R.BT;
+  Csr csr;
+  auto nd = [N](int delta) { return (N - delta + 3) * (N - delta + 2) * (N - delta + 1) / 6; };
+  double fl = 9.0 * B;                                     // I = c0 Q
+  for (int delta = 0; delta < N; ++delta) {
+    const int nin = nd(delta), nout = nd(delta + 1);
+    for (int x = 0; x < 3; ++x) {
+      const double* K = R.Ktilde.data() + (size_t)x * B * B;
+      s->T.ck[delta][x] = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; });
+      for (int r = 0; r < nout; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.ck[delta][x], r) + 1.0);
+    }
+    fl += nout * (2.0 * 3 * kStarSlots + 2.0 * 9);        // mixing + time integral
+  }
+  for (int x = 0; x < 3; ++x) {
+    const double* K = R.Khat.data() + (size_t)x * B * B;
+    s->T.vol[x] = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
+    for (int r = 0; r < B; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.vol[x], r) + 1.0);
+  }
+  fl += B * 2.0 * 3 * kStarSlots;
+  double fn = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    const double* Rs = R.R.data() + (size_t)f * B * BT;
+    const double* Rh = R.Rhat.data() + (size_t)f * B * BT;
+    s->T.rT[f] = csr.add(BT, B, [&](int r, int c) { return Rs[c + (size_t)r * B]; });
+    s->T.rhat[f] = csr.add(B, BT, [&](int r, int c) { return Rh[r + (size_t)c * B]; });
+    double lift = 0.0;
+    for (int r = 0; r < BT; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.rT[f], r) + 1.0);
+    for (int r = 0; r < B; ++r) lift += 9.0 * (2.0 * csr.row_nnz(s->T.rhat[f], r) + 1.0 + 1.0);
+    fl += BT * 2.0 * 81 + lift;
+    double blocks = 0.0;
+    for (int d = 0; d <= N; ++d) blocks += (d + 1.0) * (d + 1.0);
+    fn += 9.0 * 2.0 * blocks + BT * 2.0 * 81 + lift;
+  }
+  fl += 9.0 * B;                                           // Q + dQ
+  fn += 9.0 * B;
+  s->flops_local = fl;
+  s->flops_neigh = fn;
+  const double qb = 8.0 * 9 * B, pb = 8.0 * 4 * 9 * BT;
+  s->bytes_local = 3 * qb + pb + 8.0 * (3 * kStarSlots + 4 * 81);
+  s->bytes_neigh = 2 * qb + pb + 8.0 * 4 * 81 + 16.0;
+  if (csr.col.size() > 0x7fffffff) throw Error(YT_ERR_UNSUPPORTED, "tables too large");
+  s->d_rp = dalloc<int>(csr.rp.size());
+  s->d_col = dalloc<uint16_t>(csr.col.size());
+  s->d_val = dalloc<double>(csr.val.size());
+  s->d_f = dalloc<double>(R.f.size());
+  cuda_check(cudaMemcpy(s->d_rp, csr.rp.data(), csr.rp.size() * sizeof(int), cudaMemcpyHostToDevice), "copy rp");
+  cuda_check(cudaMemcpy(s->d_col, csr.col.data(), csr.col.size() * sizeof(uint16_t), cudaMemcpyHostToDevice), "copy col");
+  cuda_check(cudaMemcpy(s->d_val, csr.val.data(), csr.val.size() * sizeof(double), cudaMemcpyHostToDevice), "copy val");
+  cuda_check(cudaMemcpy(s->d_f, R.f.data(), R.f.size() * sizeof(double), cudaMemcpyHostToDevice), "copy f");
+  s->T.rp = s->d_rp;
+  s->T.col = s->d_col;
+  s->T.val = s->d_val;
+  s->T.f = s->d_f;
+  double c = 1.0;
+  for (int d = 0; d <= N && d < 8; ++d) {
+    c *= s->dt / (d + 1.0);
+    s->T.coeff[d] = c;                                     // dt^{d+1}/(d+1)!
+  }
+}
+
+unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
+                                      yt_stream stream, yt_solver** out) {
+  return guarded([&] {
+    YT_REQUIRE(mesh && scheme && out, YT_ERR_INVALID, "null argument");
+    *out = nullptr;
+    YT_REQUIRE(mesh->n_elements > 0 && mesh->material && mesh->jacobian, YT_ERR_INVALID,
+               "mesh needs n_elements > 0, material and jacobian");
+    YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
+    YT_REQUIRE(scheme->order >= 2 && scheme->order <= 7, YT_ERR_INVALID, "order must be 2..7");
+    YT_REQUIRE(scheme->precision == YT_F64, YT_ERR_UNSUPPORTED, "solver precision: YT_F64 only in this build");
+    YT_REQUIRE(scheme->order <= 6, YT_ERR_UNSUPPORTED, "FP64 solver: orders 2..6 in this build");
+    YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
+    YT_REQUIRE(mesh->n_elements < (int64_t(1) << 27), YT_ERR_UNSUPPORTED, "at most 2^27 elements");
+    const bool nb = mesh->neighbours != nullptr;
+    YT_REQUIRE(!nb || (mesh->faces && mesh->orient), YT_ERR_INVALID, "faces/orient required with neighbours");
+    auto s = std::make_unique<yt_solver>();
+    s->N = scheme->order - 1;
+    s->B = n_basis(s->N);
+    s->BT = n_face_basis(s->N);
+    s->E = mesh->n_elements;
+    s->ntiles = (s->E + kTile - 1) / kTile;
+    s->Epad = s->ntiles * kTile;
+    s->prec = scheme->precision;
+    s->dt = scheme->dt;
+    s->has_neighbours = nb;
+    std::vector<int> conn;
+    if (nb) {
+      conn.assign((size_t)s->Epad * 4, 0);
+      for (int64_t e = 0; e < s->E; ++e)
+        for (int f = 0; f < 4; ++f) {
+          const int64_t n = mesh->neighbours[e * 4 + f];
+          const int j = mesh->faces[e * 4 + f], h = mesh->orient[e * 4 + f];
+          YT_REQUIRE(n >= 0 && n < s->E, YT_ERR_INVALID, "neighbour index out of range");
+          YT_REQUIRE(j >= 0 && j < 4 && h >= 0 && h < 3, YT_ERR_INVALID, "face/orientation out of range");
+          conn[e * 4 + f] = (int)((n << 4) | (j << 2) | h);
+        }
+    }
+    build_tables(s.get());
+    dispatch_smem(s.get());
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t nq = (size_t)s->Epad * kNq * s->B;
+    s->Q = dalloc<double>(nq);
+    s->I = dalloc<double>(nq);
+    s->Pface = dalloc<double>((size_t)s->Epad * 4 * kNq * s->BT);
+    s->star = dalloc<double>((size_t)s->Epad * 3 * kStarSlots);
+    s->floc = dalloc<double>((size_t)s->Epad * 4 * 81);
+    s->fnb = dalloc<double>((size_t)s->Epad * 4 * 81);
+    s->conn = dalloc<int>((size_t)s->Epad * 4);
+    cuda_check(cudaMemsetAsync(s->Q, 0, nq * sizeof(double), st), "memset Q");
+    cuda_check(cudaMemsetAsync(s->I, 0, nq * sizeof(double), st), "memset I");
+    cuda_check(cudaMemsetAsync(s->Pface, 0, (size_t)s->Epad * 4 * kNq * s->BT * sizeof(double), st), "memset P");
+    cuda_check(cudaMemsetAsync(s->conn, 0, (size_t)s->Epad * 4 * sizeof(int), st), "memset conn");
+    if (nb) cuda_check(cudaMemcpyAsync(s->conn, conn.data(), conn.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy conn");
+    double* dmat = dalloc<double>((size_t)s->E * 3);
+    double* djac = dalloc<double>((size_t)s->E * 9);
+    cudaError_t e1 = cudaMemcpyAsync(dmat, mesh->material, (size_t)s->E * 3 * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaError_t e2 = cudaMemcpyAsync(djac, mesh->jacobian, (size_t)s->E * 9 * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaError_t e3 = cudaMemcpyToSymbolAsync(c_star, &kStar, sizeof(kStar), 0, cudaMemcpyHostToDevice, st);
+    cudaError_t e4 = cudaMemcpyToSymbolAsync(c_face_verts, kFaceVerts, sizeof(kFaceVerts), 0, cudaMemcpyHostToDevice, st);
+    if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) {
+      k_setup<<<blocks_for(s->Epad, 128), 128, 0, st>>>(dmat, djac, s->E, s->Epad, s->star, s->floc, s->fnb);
+      e1 = cudaGetLastError();
+    }
+    cudaError_t e5 = cudaStreamSynchronize(st);
+    cudaFree(dmat);
+    cudaFree(djac);
+    cuda_check(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : (e4 != cudaSuccess ? e4 : e5))),
+               "solver setup");
+    *out = s.release();
+  });
+}
+
+extern "C" yt_status yt_solver_set_dofs(yt_solver* s, const double* dofs, yt_memory where,
+                                        yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s && dofs, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(where == YT_MEM_HOST || where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)s->E * kNq * s->B;
+    const double* src = dofs;
+    if (where == YT_MEM_HOST) {
+      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+      cuda_check(cudaMemcpyAsync(s->staging, dofs, n * sizeof(double), cudaMemcpyHostToDevice, st), "H2D dofs");
+      src = s->staging;
+    }
+    const int64_t total = s->Epad * kNq * s->B;
+    k_to_blocked<<<blocks_for(total, 256), 256, 0, st>>>(src, s->Q, s->E, s->Epad, s->B);
+    cuda_check(cudaGetLastError(), "k_to_blocked");
+  });
+}
+
+extern "C" yt_status yt_solver_get(yt_solver* s, yt_field field, double* out, yt_memory where,
+                                   yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s && out, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(field == YT_FIELD_DOFS || field == YT_FIELD_TIME_INTEGRAL, YT_ERR_INVALID, "field");
+    YT_REQUIRE(where == YT_MEM_HOST || where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)s->E * kNq * s->B;
+    double* dst = out;
+    if (where == YT_MEM_HOST) {
+      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+      dst = s->staging;
+    }
+    k_from_blocked<<<blocks_for((int64_t)n, 256), 256, 0, st>>>(field == YT_FIELD_DOFS ? s->Q : s->I,
+                                                                 dst, s->E, s->B);
+    cuda_check(cudaGetLastError(), "k_from_blocked");
+    if (where == YT_MEM_HOST)
+      cuda_check(cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+  });
+}
+
+extern "C" yt_status yt_step_local(yt_solver* s, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    dispatch_local(s, reinterpret_cast<cudaStream_t>(stream));
+  });
+}
+
+extern "C" yt_status yt_step_neighbour(yt_solver* s, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
+    dispatch_neigh(s, reinterpret_cast<cudaStream_t>(stream));
+  });
+}
+
+extern "C" yt_status yt_step(yt_solver* s, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    dispatch_local(s, st);
+    dispatch_neigh(s, st);
+  });
+}
+
+extern "C" yt_status yt_solver_stats(const yt_solver* s, double* lf, double* nf, double* lb,
+                                     double* nbb) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    if (lf) *lf = s->flops_local;
+    if (nf) *nf = s->flops_neigh;
+    if (lb) *lb = s->bytes_local;
+    if (nbb) *nbb = s->bytes_neigh;
+  });
+}
+
+namespace {
+void copy_reference(int N, const char* name, double* out, int64_t* count) {
+  YT_REQUIRE(name && count, YT_ERR_INVALID, "null argument");
+  const RefMatrices& R = reference_matrices(N);
+  const std::vector<double>* v = nullptr;
+  const std::string nm(name);
+  if (nm == "M") v = &R.M;
+  else if (nm == "Khat") v = &R.Khat;
+  else if (nm == "Ktilde") v = &R.Ktilde;
+  else if (nm == "R") v = &R.R;
+  else if (nm == "Rhat") v = &R.Rhat;
+  else if (nm == "f") v = &R.f;
+  else if (nm == "W") v = &R.W;
+  YT_REQUIRE(v, YT_ERR_INVALID, "unknown matrix name");
+  *count = (int64_t)v->size();
+  if (out) std::memcpy(out, v->data(), v->size() * sizeof(double));
+}
+}  // namespace
+
+extern "C" yt_status yt_solver_reference_matrix(const yt_solver* s, const char* name,
+                                                double* out, int64_t* count) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    copy_reference(s->N, name, out, count);
+  });
+}
+
+extern "C" yt_status yt_reference_matrix(int32_t order, const char* name, double* out,
+                                         int64_t* count) {
+  return guarded([&] {
+    YT_REQUIRE(order >= 2 && order <= 7, YT_ERR_INVALID, "order must be 2..7");
+    copy_reference(order - 1, name, out, count);
+  });
+}
+
+extern "C" void yt_solver_destroy(yt_solver* s) { delete s; }

@@ -1,0 +1,123 @@
+"""Python view of the ADER-DG solver of the C ABI (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _stream_handle(stream) -> int | None:
+    """A CUDA stream handle from a torch.cuda.Stream, an int, or None (default stream)."""
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Solver:
+    """One elastic ADER-DG problem resident on the device.
+
+    material (E,3) rho/lambda/mu; jacobian (E,3,3) dx/dxi; neighbours/faces/orient (E,4)
+    or None.  DOFs are exchanged in the canonical layout [element][quantity][basis]."""
+
+    def __init__(self, order, dt, material, jacobian, neighbours=None, faces=None,
+                 orient=None, precision=_lib.YT_F64, stream=None):
+        self.lib = _lib.load()
+        E = int(np.asarray(material).shape[0])
+        self.n_elements = E
+        self.order = int(order)
+        self._mat = np.ascontiguousarray(material, dtype=np.float64).reshape(E, 3)
+        # column-major 3x3 per element: entry (i, c) at i + 3c
+        self._jac = np.ascontiguousarray(np.asarray(jacobian, dtype=np.float64).reshape(E, 3, 3)
+                                         .transpose(0, 2, 1)).reshape(E, 9)
+        desc = _lib.MeshDesc()
+        desc.n_elements = E
+        desc.material = _ptr(self._mat, C.c_double)
+        desc.jacobian = _ptr(self._jac, C.c_double)
+        if neighbours is not None:
+            self._nb = np.ascontiguousarray(neighbours, dtype=np.int32)
+            self._fj = np.ascontiguousarray(faces, dtype=np.int8)
+            self._fh = np.ascontiguousarray(orient, dtype=np.int8)
+            desc.neighbours = _ptr(self._nb, C.c_int32)
+            desc.faces = _ptr(self._fj, C.c_int8)
+            desc.orient = _ptr(self._fh, C.c_int8)
+        sch = _lib.SchemeDesc(order=self.order, dt=float(dt), precision=precision, flags=0)
+        handle = C.c_void_p()
+        _lib.check(self.lib.yt_solver_create(C.byref(desc), C.byref(sch),
+                                             _stream_handle(stream), C.byref(handle)),
+                   "yt_solver_create")
+        self.handle = handle
+        self.n_basis = (self.order) * (self.order + 1) * (self.order + 2) // 6
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.yt_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ data movement
+    def set_dofs_host(self, Q, stream=None):
+        """Q as numpy (E, B, 9) [element, basis, quantity] (the oracle's layout)."""
+        canon = np.ascontiguousarray(np.asarray(Q, dtype=np.float64).transpose(0, 2, 1))
+        self._host_in = canon
+        _lib.check(self.lib.yt_solver_set_dofs(self.handle, canon.ctypes.data, _lib.YT_MEM_HOST,
+                                               _stream_handle(stream)), "yt_solver_set_dofs")
+
+    def set_dofs_ptr(self, ptr: int, where: int, stream=None):
+        _lib.check(self.lib.yt_solver_set_dofs(self.handle, ptr, where, _stream_handle(stream)),
+                   "yt_solver_set_dofs")
+
+    def get_ptr(self, field: int, ptr: int, where: int, stream=None):
+        _lib.check(self.lib.yt_solver_get(self.handle, field, ptr, where, _stream_handle(stream)),
+                   "yt_solver_get")
+
+    def get_host(self, field=_lib.YT_FIELD_DOFS, stream=None, sync=True):
+        """Field as numpy (E, B, 9); synchronises the device when sync is True."""
+        out = np.empty((self.n_elements, 9, self.n_basis))
+        _lib.check(self.lib.yt_solver_get(self.handle, field, out.ctypes.data, _lib.YT_MEM_HOST,
+                                          _stream_handle(stream)), "yt_solver_get")
+        if sync:
+            import torch
+            torch.cuda.synchronize()
+        return out.transpose(0, 2, 1)
+
+    # ------------------------------------------------------------------------ compute
+    def step(self, stream=None):
+        _lib.check(self.lib.yt_step(self.handle, _stream_handle(stream)), "yt_step")
+
+    def step_local(self, stream=None):
+        _lib.check(self.lib.yt_step_local(self.handle, _stream_handle(stream)), "yt_step_local")
+
+    def step_neighbour(self, stream=None):
+        _lib.check(self.lib.yt_step_neighbour(self.handle, _stream_handle(stream)),
+                   "yt_step_neighbour")
+
+    def stats(self):
+        v = [C.c_double() for _ in range(4)]
+        _lib.check(self.lib.yt_solver_stats(self.handle, *[C.byref(x) for x in v]),
+                   "yt_solver_stats")
+        return dict(local_flops=v[0].value, neighbour_flops=v[1].value,
+                    local_bytes=v[2].value, neighbour_bytes=v[3].value)
+
+
+def reference_matrix(order: int, name: str) -> np.ndarray:
+    """Host-side reference matrix of the library (no device work)."""
+    lib = _lib.load()
+    n = C.c_int64()
+    _lib.check(lib.yt_reference_matrix(order, name.encode(), None, C.byref(n)), "yt_reference_matrix")
+    out = np.empty(n.value)
+    _lib.check(lib.yt_reference_matrix(order, name.encode(), _ptr(out, C.c_double), C.byref(n)),
+               "yt_reference_matrix")
+    return out

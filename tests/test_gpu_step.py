@@ -1,0 +1,125 @@
+"""Parity of the CUDA ADER-DG step (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative Frobenius norm per quantity <= 1e-12 (FP64; the paper compares the
+optimised and the naive kernel by the Frobenius norm of the difference, Sec. 4.9)."""
+import numpy as np
+import pytest
+
+import workload as wl
+from oracle import basis, planewave, scheme
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def yt():
+    import paper_1903_11521_gb300 as yt
+    yt.load()
+    return yt
+
+
+def rel_per_quantity(a, b):
+    num = np.sqrt(((a - b) ** 2).sum(axis=(0, 1)))
+    den = np.sqrt((b ** 2).sum(axis=(0, 1)))
+    return num / den
+
+
+def make_case(E, order, scale, seed=1903):
+    N = order - 1
+    el = wl.random_elements(E, seed=seed)
+    conn = wl.random_connectivity(E, seed=seed + 2)
+    Q = wl.random_dofs(E, basis.n_basis(N), seed=seed + 1, scale=scale, elements=el)
+    dt = wl.cfl_time_step(el, N)
+    return el, conn, Q, dt
+
+
+def run_gpu(yt, el, conn, Q, dt, order, full=True):
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    s = yt.Solver(order, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient)
+    s.set_dofs_host(Q)
+    if full:
+        s.step()
+    else:
+        s.step_local()
+    q = s.get_host(yt.YT_FIELD_DOFS)
+    i = s.get_host(yt.YT_FIELD_TIME_INTEGRAL)
+    s.close()
+    return q, i
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("E", [1, 37, 100])
+def test_local_step_parity(yt, order, E):
+    """K_local alone (derivatives, time integral, volume, local flux) — the O4 / 1000-tet
+    local update is this test at larger E."""
+    if E == 1:
+        E = 2
+    el, conn, Q, dt = make_case(E, order, "impedance")
+    q_gpu, i_gpu = run_gpu(yt, el, conn, Q, dt, order, full=False)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    _, I = scheme.derivatives_and_time_integral(Q, star, dt, order - 1)
+    q_ref = scheme.local_update(Q, I, star, loc, order - 1)
+    assert rel_per_quantity(i_gpu, I).max() < TOL
+    assert rel_per_quantity(q_gpu, q_ref).max() < TOL
+    assert rel_per_quantity(q_gpu - Q, q_ref - Q).max() < 1e-11
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
+def test_full_step_parity(yt, order):
+    E = 70
+    el, conn, Q, dt = make_case(E, order, "impedance", seed=7)
+    q_gpu, i_gpu = run_gpu(yt, el, conn, Q, dt, order, full=True)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    q_ref, I = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
+                                dt, order - 1)
+    assert rel_per_quantity(i_gpu, I).max() < TOL
+    assert rel_per_quantity(q_gpu, q_ref).max() < TOL
+    assert rel_per_quantity(q_gpu - Q, q_ref - Q).max() < 1e-11
+
+
+def test_config1_local_update_unit_dofs(yt):
+    """Order 4, 1000 tets, N(0,1) DOFs, one local update."""
+    el, conn, Q, dt = make_case(1000, 4, "unit")
+    q_gpu, i_gpu = run_gpu(yt, el, conn, Q, dt, 4, full=False)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    _, I = scheme.derivatives_and_time_integral(Q, star, dt, 3)
+    q_ref = scheme.local_update(Q, I, star, loc, 3)
+    assert rel_per_quantity(i_gpu, I).max() < TOL
+    assert rel_per_quantity(q_gpu, q_ref).max() < TOL
+
+
+def test_plane_wave_on_device(yt):
+    """Several steps on the periodic mesh: matches the oracle step by step and converges
+    to the closed-form plane wave like the oracle does."""
+    order, N = 3, 2
+    k = 2 * np.pi * np.array([1.0, 1.0, 0.0])
+    mesh = wl.periodic_cube_mesh(4)
+    el = mesh.elements
+    T = 0.03
+    steps = int(np.ceil(T / wl.cfl_time_step(el, N, cfl=0.3)))
+    dt = T / steps
+    Q0 = planewave.project(mesh, N, 0.0, k, 1.0, 2.0, 1.0)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    s = yt.Solver(order, dt, mat, el.jac, mesh.conn.neighbours, mesh.conn.faces, mesh.conn.orient)
+    s.set_dofs_host(Q0)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    Q = Q0
+    for _ in range(steps):
+        s.step()
+        Q, _ = scheme.ader_step(Q, star, loc, nb, mesh.conn.neighbours, mesh.conn.faces,
+                                mesh.conn.orient, dt, N)
+    q_gpu = s.get_host()
+    s.close()
+    assert rel_per_quantity(q_gpu, Q).max() < 1e-11
+    err_gpu = planewave.l2_error(mesh, N, q_gpu, T, k, 1.0, 2.0, 1.0)
+    err_ora = planewave.l2_error(mesh, N, Q, T, k, 1.0, 2.0, 1.0)
+    assert np.allclose(err_gpu, err_ora, rtol=1e-6)
+    assert err_gpu[6] < 0.05
+
+
+def test_deterministic(yt):
+    el, conn, Q, dt = make_case(64, 5, "unit", seed=3)
+    a, _ = run_gpu(yt, el, conn, Q, dt, 5)
+    b, _ = run_gpu(yt, el, conn, Q, dt, 5)
+    assert np.array_equal(a, b)
