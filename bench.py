@@ -1,0 +1,385 @@
+"""Benchmark: element-updates/s of one full elastic ADER-DG step at order 6 on 1,000,000
+tetrahedra (CK derivatives + time integral + volume + local flux + neighbour flux), FP64,
+synthetic SeisSol-reproducer-like inputs (random material, random affine elements, random
+face matching with random orientations, DOFs ~ N(0,1)).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is device-resident throughput (inputs in HBM);
+`e2e` runs the same step through the C ABI with host buffers (H2D of Q, step, D2H of Q).
+`--impl reference` times the FP64 oracle on the host cores on a bounded sample.
+Under torchrun (N > 1) every rank solves its own independent problem of the same size
+(weak scaling, no data-path collective); the timed region is bracketed by barriers and the
+maximum time over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload as wl  # noqa: E402
+
+ORDER = 6
+N_ELEMENTS = 1_000_000
+METRIC = "element-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA peak derived from the unit counts and clocks of the part: 152 SMs x 2 FP64 FMA
+# per clock per SM x 2 flop x 2070 MHz = 1.2586 TFLOP/s (nominal FP64: 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
+# it was captured on (see profiles/k_local_o6_fp64_40k.md)
+NCU_TRAFFIC_PER_ELEMENT = {"167e58dde606798c": {6: (336.535808e6 + 506.209792e6) / 40000}}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=N_ELEMENTS)
+    ap.add_argument("--order", type=int, default=ORDER)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, extra=None):
+    cfg = {"workload": f"elastic ADER-DG full step, order {args.order} "
+                       f"(B={(args.order) * (args.order + 1) * (args.order + 2) // 6} x 9 quantities), "
+                       f"{args.elements} tets, random 4-regular face matching",
+           "order": args.order, "elements": args.elements, "quantities": 9,
+           "precision": "fp64", "seed": wl.SEED,
+           "l2": "per-step working set (Q, I, face projections: ~14 GB) exceeds the 129 MB L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------- clocks sampler
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- oracle baseline
+def _oracle_local(args):
+    from oracle import scheme
+    Q, star, loc, dt, N = args
+    _, I = scheme.derivatives_and_time_integral(Q, star, dt, N)
+    return scheme.local_update(Q, I, star, loc, N), I
+
+
+def _oracle_neigh(args):
+    from oracle import scheme
+    Qp, I, fnb, nb, fj, fh, N = args
+    return scheme.neighbour_update(Qp, I, fnb, nb, fj, fh, N)
+
+
+class OracleStep:
+    """The FP64 oracle step (oracle.scheme, unmodified) over a sample of the workload,
+    spread over the host cores by a spawn-started process pool (chunks of elements)."""
+
+    def __init__(self, n_sample: int, order: int, workers: int):
+        from oracle import basis, scheme
+        N = order - 1
+        self.N = N
+        self.E = n_sample
+        el = wl.random_elements(n_sample)
+        self.conn = wl.random_connectivity(n_sample)
+        self.Q = wl.random_dofs(n_sample, basis.n_basis(N), elements=el)
+        self.dt = wl.cfl_time_step(el, N)
+        self.star, self.loc, self.fnb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+        basis.float_matrices(N)
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(N,))
+        self.chunks = np.array_split(np.arange(n_sample), workers)
+
+    def step(self):
+        c = self.chunks
+        res = self.pool.map(_oracle_local, [(self.Q[i], self.star[i], self.loc[i], self.dt, self.N) for i in c])
+        Qp = np.concatenate([r[0] for r in res])
+        I = np.concatenate([r[1] for r in res])
+        # each chunk receives the time integrals of its own neighbours only
+        jobs = []
+        for i in c:
+            nb = self.conn.neighbours[i]
+            local_ids = np.arange(nb.size, dtype=np.int64).reshape(nb.shape)
+            jobs.append((Qp[i], I[nb.ravel()], self.fnb[i], local_ids,
+                         self.conn.faces[i], self.conn.orient[i], self.N))
+        res2 = self.pool.map(_oracle_neigh, jobs)
+        return np.concatenate(res2)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _pool_init(N):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import basis
+    basis.float_matrices(N)
+
+
+def oracle_rate(order, target_s=12.0, workers=None):
+    """Oracle element-updates/s on a sample sized for ~target_s seconds of CPU work."""
+    workers = workers or os.cpu_count() or 1
+    n = 256 * workers
+    probe = OracleStep(n, order, workers)
+    probe.step()
+    t0 = time.perf_counter()
+    probe.step()
+    t = time.perf_counter() - t0
+    probe.close()
+    n2 = int(min(200_000, max(n, n * target_s / max(t, 1e-3))))
+    runner = OracleStep(n2, order, workers)
+    t0 = time.perf_counter()
+    runner.step()
+    t = time.perf_counter() - t0
+    runner.close()
+    return n2 / t, n2, t, workers
+
+
+# ------------------------------------------------------------------------ GPU bench
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    import paper_1903_11521_gb300 as yt
+
+    N = args.order - 1
+    B = args.order * (args.order + 1) * (args.order + 2) // 6
+    E = args.elements
+    seed = wl.SEED + 1000 * rank
+    el = wl.random_elements(E, seed=seed)
+    conn = wl.random_connectivity(E, seed=seed + 2)
+    Q = wl.random_dofs(E, B, seed=seed + 1)
+    dt = wl.cfl_time_step(el, N)
+    stream = torch.cuda.current_stream()
+    solver = yt.Solver(args.order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac,
+                       conn.neighbours, conn.faces, conn.orient, stream=stream)
+    solver.set_dofs_host(Q, stream=stream)
+    torch.cuda.synchronize()
+    stats = solver.stats()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.step(stream=stream)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    barrier()
+    for k in range(K):
+        ev[k][0].record(stream)
+        solver.step_local(stream=stream)
+        ev[k][1].record(stream)
+        solver.step_neighbour(stream=stream)
+        ev[k][2].record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[K - 1][2])
+    local_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    neigh_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    t_max = total_ms
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * E * K / (t_max / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), H2D + step + D2H per step
+    e2e = None
+    if not args.no_e2e:
+        canon = torch.empty((E, 9, B), dtype=torch.float64, pin_memory=True)
+        canon.numpy()[:] = Q.transpose(0, 2, 1)
+        out = torch.empty_like(canon, pin_memory=True)
+        for _ in range(2):
+            solver.set_dofs_ptr(canon.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+            solver.step(stream=stream)
+            solver.get_ptr(yt.YT_FIELD_DOFS, out.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            solver.set_dofs_ptr(canon.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+            solver.step(stream=stream)
+            solver.get_ptr(yt.YT_FIELD_DOFS, out.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+        b.record(stream)
+        barrier()
+        e_ms = a.elapsed_time(b)
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        nbytes = E * 9 * B * 8
+        e2e = {"value": ws * E * K / (e_ms / 1e3), "unit": METRIC,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": e_ms / K}
+    solver.close()
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    flops_local = stats["local_flops"] * E
+    achieved = flops_local / (local_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_local (derivatives + time integral + volume + local flux)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
+                "traffic": None,
+                "k_neigh_frac": stats["neighbour_flops"] * E / (neigh_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                "step_frac": (stats["local_flops"] + stats["neighbour_flops"]) * E / (total_ms / K / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                "flops_per_element": {"local": stats["local_flops"], "neighbour": stats["neighbour_flops"]}}
+    # DRAM bytes per element of k_local from one ncu capture of a 40,000-tet case, valid
+    # only for the kernel source it was taken on (scaled to E: traffic grows with E)
+    src = os.path.join(ROOT, "paper_1903_11521_gb300", "csrc", "ader_kernels.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if args.order in NCU_TRAFFIC_PER_ELEMENT.get(digest, {}):
+        roofline["traffic"] = NCU_TRAFFIC_PER_ELEMENT[digest][args.order] * E
+        roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, scaled)"
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        rate, n_s, t_s, cores = oracle_rate(args.order)
+        cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "sample": f"{n_s} elements of the same workload recipe, one full step "
+                         f"({t_s:.1f} s), dense unfactorised FP64 oracle"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
+            "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": 2 * K,
+            "kernel_ms": {"k_local": local_ms, "k_neigh": neigh_ms},
+            "context": {"paper_skx_dp_o6_element_updates_per_s": 1244e6 / (56 * 9),
+                        "paper_hardware": "2x Xeon Platinum 8174 (SKX), App. A"}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    workers = os.cpu_count() or 1
+    # size one step of the oracle for ~8 s on the host cores
+    rate, _, _, _ = oracle_rate(args.order, target_s=3.0, workers=workers)
+    n = int(max(256 * workers, min(200_000, rate * 8.0)))
+    runner = OracleStep(n, args.order, workers)
+    for _ in range(args.warmup):
+        runner.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        runner.step()
+    t = time.perf_counter() - t0
+    runner.close()
+    value = n * args.steps / t
+    sample = (f"{n} elements of the same workload recipe per step (the full problem has "
+              f"{args.elements}); dense unfactorised FP64 oracle, spawn pool of {workers} processes")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": workers, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
