@@ -83,7 +83,9 @@ const char* yt_version(void);
  * the operation-minimal binary tree under the sparse cost of Sec. 4.3, the index
  * permutations of the temporaries by the dynamic program of Sec. 4.5 (Eqs. permopt,
  * permcost, subproblem) with the Loop-over-GEMM cost (s, l+r, -f), and the non-zero flop
- * count.
+ * count.  A stored value 0.0 of a global constant is treated as a structural zero.
+ * yt_plan_create, yt_plan_stats_get and yt_plan_eqspp run on the host only; the plan's
+ * device tables are created by its first yt_execute_batched.
  */
 typedef struct yt_tensor_desc {
   const char* name;         /* as used in the expression */
@@ -102,8 +104,11 @@ typedef struct yt_plan_stats {
   int64_t bytes_per_element; /* per-element tensor bytes read + written */
   int32_t n_ops;             /* binary operations after strength reduction */
   int32_t n_terms;
-  char order[1024];          /* parenthesised contraction order, e.g.
-                                "((B*w)_k*A)_l" ; temporaries' index orders appended */
+  int64_t log_cost[4];       /* Loop-over-GEMM cost (s, l+r, -f, l) of the chosen index
+                                orders, summed over all binary nodes of all terms */
+  char order[1024];          /* the trees, e.g. "sum_l(A[lj]*sum_k(B[ikl]*w[k])[il])[ij]":
+                                "sum_x(L*R)[o]" multiplies L and R, sums the indices x and
+                                stores the result in index order o */
 } yt_plan_stats;
 
 struct yt_plan;

@@ -23,7 +23,7 @@ class TensorDesc(C.Structure):
 class PlanStats(C.Structure):
     _fields_ = [("nz_flops", C.c_double), ("hw_flops", C.c_double), ("naive_flops", C.c_double),
                 ("bytes_per_element", C.c_int64), ("n_ops", C.c_int32), ("n_terms", C.c_int32),
-                ("order", C.c_char * 1024)]
+                ("log_cost", C.c_int64 * 4), ("order", C.c_char * 1024)]
 
 
 class MeshDesc(C.Structure):

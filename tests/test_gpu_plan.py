@@ -1,0 +1,158 @@
+"""Parity of the batched executor (yt_execute_batched, through the C ABI) with the oracle:
+random Einstein expressions against the brute-force Eq. gentensorop, and the four SeisSol
+kernels (Sec. 5.1.1) written as expressions against the direct oracle."""
+import numpy as np
+import pytest
+
+import workload as wl
+from oracle import basis, scheme
+from oracle import einsum as es
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def yt():
+    import paper_1903_11521_gb300 as yt
+    yt.load()
+    return yt
+
+
+def to_dev(arr, dtype):
+    import torch
+    from paper_1903_11521_gb300 import element_major
+    return torch.from_numpy(element_major(arr).astype(dtype)).cuda()
+
+
+def from_dev(t, shape):
+    from paper_1903_11521_gb300 import from_element_major
+    return from_element_major(t.cpu().numpy().astype(np.float64), shape)
+
+
+def run(yt, expr, consts, per_elem, out_name, out_shape, E, precision=0, out_init=None):
+    import torch
+    dtype = np.float64 if precision == 0 else np.float32
+    tensors = []
+    dev = {}
+    for name, arr in per_elem.items():
+        tensors.append((name, arr.shape[1:], None, None))
+        dev[name] = to_dev(arr, dtype)
+    init = out_init if out_init is not None else np.full((E,) + out_shape, 7.0)
+    tensors.append((out_name, out_shape, None, None))
+    dev[out_name] = to_dev(init, dtype)
+    for name, (val, pat) in consts.items():
+        tensors.append((name, val.shape, pat, val))
+    plan = yt.Plan(expr, tensors, precision=precision)
+    plan.execute(dev, E)
+    torch.cuda.synchronize()
+    return from_dev(dev[out_name], out_shape), plan
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("E", [1, 37])
+def test_random_expressions(yt, seed, E):
+    rng = np.random.default_rng(seed)
+    sizes = {'i': 3, 'j': 2, 'k': 4, 'l': 3, 'm': 2}
+    A = rng.standard_normal((sizes['i'], sizes['k'])) * (rng.random((3, 4)) < 0.7)
+    Bp = rng.standard_normal((E, sizes['k'], sizes['j'], sizes['l']))
+    w = rng.standard_normal((E, sizes['l'], sizes['m']))
+    out, plan = run(yt, "U[imj] = 0.5 * A[ik] * B[kjl] * w[lm]", {'A': (A, None)},
+                    {'B': Bp, 'w': w}, 'U', (3, 2, 2), E)
+    for e in range(E):
+        ref = 0.5 * es.einsum_bruteforce('imj', [('ik', A), ('kjl', Bp[e]), ('lm', w[e])])
+        assert np.allclose(out[e], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_accumulate_and_assign(yt):
+    rng = np.random.default_rng(5)
+    E = 40
+    X = rng.standard_normal((E, 4, 3))
+    K = rng.standard_normal((5, 4))
+    init = rng.standard_normal((E, 5, 3))
+    out, _ = run(yt, "Y[ap] += K[ab] * X[bp] + 2.0 * K[ab] * X[bp]", {'K': (K, None)}, {'X': X}, 'Y',
+                 (5, 3), E, out_init=init)
+    assert np.allclose(out, init + 3.0 * np.einsum('ab,ebp->eap', K, X), rtol=1e-13, atol=1e-12)
+    out, _ = run(yt, "Y[ap] = K[ab] * X[bp]", {'K': (K, None)}, {'X': X}, 'Y', (5, 3), E, out_init=init)
+    assert np.allclose(out, np.einsum('ab,ebp->eap', K, X), rtol=1e-13, atol=1e-12)
+    # transposed copy (single factor)
+    out, _ = run(yt, "Z[pb] = X[bp]", {}, {'X': X}, 'Z', (3, 4), E)
+    assert np.array_equal(out, X.transpose(0, 2, 1))
+
+
+def _seissol_inputs(order, E):
+    N = order - 1
+    el = wl.random_elements(E, seed=11)
+    conn = wl.random_connectivity(E, seed=12)
+    Q = wl.random_dofs(E, basis.n_basis(N), seed=13, scale="impedance", elements=el)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    return N, Q, star, loc, nb, conn
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_seissol_kernels_as_expressions(yt, order):
+    E = 45
+    N, Q, star, loc, nb, conn = _seissol_inputs(order, E)
+    m = basis.float_matrices(N)
+    B, Bt = basis.n_basis(N), basis.n_face_basis(N)
+    As = {f"A{x}": star[:, x] for x in range(3)}
+    # derivative (Eq. seissol:derivative)
+    consts = {f"K{x}": (m['Ktilde'][x], None) for x in range(3)}
+    out, plan = run(yt, "D[kp] = K0[kl]*Q[lq]*A0[pq] + K1[kl]*Q[lq]*A1[pq] + K2[kl]*Q[lq]*A2[pq]",
+                    consts, {'Q': Q, **As}, 'D', (B, 9), E)
+    ref = sum(np.matmul(np.matmul(m['Ktilde'][x], Q), np.swapaxes(star[:, x], -1, -2)) for x in range(3))
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert plan.stats()['n_terms'] == 3
+    # volume (Eq. seissol:correction_local, first part)
+    consts = {f"K{x}": (m['Khat'][x], None) for x in range(3)}
+    out, _ = run(yt, "V[kp] += K0[kl]*I[lq]*A0[pq] + K1[kl]*I[lq]*A1[pq] + K2[kl]*I[lq]*A2[pq]",
+                 consts, {'I': Q, **As}, 'V', (B, 9), E, out_init=Q)
+    ref = Q + sum(np.matmul(np.matmul(m['Khat'][x], Q), np.swapaxes(star[:, x], -1, -2)) for x in range(3))
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    # local flux of face 2 (Rhat R^T)
+    s = 2
+    consts = {'Rh': (m['Rhat'][s], None), 'R': (m['R'][s], None)}
+    out, _ = run(yt, "F[kp] = Rh[km] * R[lm] * I[lq] * Al[pq]", consts, {'I': Q, 'Al': loc[:, s]},
+                 'F', (B, 9), E)
+    ref = np.matmul(np.matmul(m['FmHat'][s], Q), np.swapaxes(loc[:, s], -1, -2))
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    # neighbour flux of face 1 for fixed (j, h) = (3, 2), neighbour DOFs gathered
+    j, h = 3, 2
+    Inb = Q[conn.neighbours[:, 1]]
+    consts = {'Rh': (m['Rhat'][1], None), 'f': (m['f'][h], None), 'R': (m['R'][j], None)}
+    out, plan = run(yt, "G[kp] = Rh[km] * f[mn] * R[ln] * J[lq] * An[pq]", consts,
+                    {'J': Inb, 'An': nb[:, 1]}, 'G', (B, 9), E)
+    ref = np.matmul(np.matmul(m['FpHat'][1, j, h], Inb), np.swapaxes(nb[:, 1], -1, -2))
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_single_precision_plan(yt):
+    E = 64
+    N, Q, star, loc, nb, conn = _seissol_inputs(4, E)
+    m = basis.float_matrices(N)
+    B = basis.n_basis(N)
+    out, _ = run(yt, "V[kp] = K0[kl]*I[lq]*A0[pq]", {'K0': (m['Khat'][0], None)},
+                 {'I': Q, 'A0': star[:, 0]}, 'V', (B, 9), E, precision=1)
+    ref = np.matmul(np.matmul(m['Khat'][0], Q), np.swapaxes(star[:, 0], -1, -2))
+    assert np.linalg.norm(out - ref) <= 2e-6 * np.linalg.norm(ref)
+
+
+def test_many_elements_sampled(yt):
+    """100,003 elements (several grid-stride passes per warp slot), sampled checks."""
+    rng = np.random.default_rng(9)
+    E = 100_003
+    K = rng.standard_normal((6, 5))
+    X = rng.standard_normal((E, 5, 4))
+    out, _ = run(yt, "Y[ap] = K[ab] * X[bp]", {'K': (K, None)}, {'X': X}, 'Y', (6, 4), E)
+    idx = rng.integers(0, E, 200).tolist() + [0, E - 1]
+    ref = np.einsum('ab,ebp->eap', K, X[idx])
+    assert np.allclose(out[idx], ref, rtol=1e-13, atol=1e-12)
+
+
+def test_zero_elements_is_a_no_op(yt):
+    import torch
+    plan = yt.Plan("Y[ap] = K[ab] * X[bp]", [('K', (2, 2), None, np.eye(2)), ('X', (2, 2), None, None),
+                                             ('Y', (2, 2), None, None)])
+    y = torch.full((4,), 3.0, dtype=torch.float64, device='cuda')
+    plan.execute({'X': y, 'Y': y}, 0)
+    torch.cuda.synchronize()
+    assert (y == 3.0).all()
