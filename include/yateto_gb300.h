@@ -128,6 +128,23 @@ yt_status yt_plan_eqspp(const struct yt_plan* plan, int32_t term, int32_t tensor
  * for "+=".  Scratch for temporaries is allocated by the plan on first use. */
 yt_status yt_execute_batched(const struct yt_plan* plan, void* const* element_tensors,
                              int64_t n_elements, yt_stream stream);
+/* Allocation-free variant of yt_execute_batched (the paper has no counterpart).
+ * For callers that must not allocate device memory themselves or through libraries they
+ * call: code whose device memory is owned by a host framework's own pool, or loops that
+ * must not take the device-wide synchronisation that cudaMalloc / cudaFree can imply.
+ * Same arguments and results as yt_execute_batched.  It calls no cudaMalloc, cudaFree or
+ * allocating routine: the plan's operation list, index lists, constants and the
+ * temporaries live in fixed arrays inside the library (reserved on every device that
+ * loads it, until process exit): temporaries 32 MiB, index lists 2^20 integers, 4096
+ * operations, constants 2 MiB.  A plan beyond any of these limits is rejected with
+ * YT_ERR_UNSUPPORTED and a message naming the limit; nothing runs then.  The first call
+ * on each device looks up the arrays' device addresses (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call copies the
+ * plan's tables into the shared arrays (from host memory, on `stream`) and then runs the
+ * kernel; calls whose work overlaps on the device, e.g. on two streams, race on the
+ * shared arrays and must be serialised by the caller. */
+yt_status yt_execute_batched_noalloc(const struct yt_plan* plan, void* const* element_tensors,
+                                     int64_t n_elements, yt_stream stream);
 void yt_plan_destroy(struct yt_plan* plan);
 
 /* ===================================================================== solver

@@ -51,6 +51,7 @@ SIGNATURES = {
     "yt_plan_stats_get": (C.c_int, [_P, C.POINTER(PlanStats)]),
     "yt_plan_eqspp": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_uint8)]),
     "yt_execute_batched": (C.c_int, [_P, C.POINTER(_P), C.c_int64, _P]),
+    "yt_execute_batched_noalloc": (C.c_int, [_P, C.POINTER(_P), C.c_int64, _P]),
     "yt_plan_destroy": (None, [_P]),
     "yt_solver_create": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(SchemeDesc), _P, C.POINTER(_P)]),
     "yt_solver_set_dofs": (C.c_int, [_P, _P, C.c_int, _P]),

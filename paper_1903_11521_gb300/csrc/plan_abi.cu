@@ -381,3 +381,106 @@ extern "C" yt_status yt_execute_batched(const yt_plan* p, void* const* element_t
 }
 
 extern "C" void yt_plan_destroy(yt_plan* p) { delete p; }
+
+// ------------------------------------------------------ allocation-free execution
+// yt_execute_batched_noalloc runs the same executor kernel as yt_execute_batched, but
+// every device buffer it needs lives in the fixed-size file-scope arrays below, so the
+// call never allocates device memory.  The arrays are reserved on every device that
+// loads this library and stay reserved until the process exits.  All calls share them:
+// each call first copies the plan's operation list, index lists and constants into
+// them, and the temporaries are written before they are read, so nothing has to start
+// at zero.  Two calls whose work overlaps on the device (different streams, or devices
+// sharing nothing but this process) race on these arrays.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // temporaries: 32 MiB
+constexpr size_t kNoAllocProgInts = size_t(1) << 20;        // index lists: 4 MiB
+constexpr size_t kNoAllocOps = 4096;                         // operations: 256 KiB
+constexpr size_t kNoAllocConstDoubles = size_t(1) << 18;    // constants: 2 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) int g_noalloc_prog[kNoAllocProgInts];
+static __device__ __align__(256) ExecOp g_noalloc_ops[kNoAllocOps];
+static __device__ __align__(256) double g_noalloc_consts[kNoAllocConstDoubles];
+
+// Device addresses of the arrays, looked up once per device with that device current.
+struct NoAllocAddrs {
+  bool ready = false;
+  void* scratch = nullptr;
+  void* prog = nullptr;
+  void* ops = nullptr;
+  void* consts = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoAllocAddrs g_noalloc_addrs[64];
+
+NoAllocAddrs noalloc_addrs(int dev) {
+  YT_REQUIRE(dev >= 0 && dev < 64, YT_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocAddrs& a = g_noalloc_addrs[dev];
+  if (!a.ready) {
+    cuda_check(cudaGetSymbolAddress(&a.scratch, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+    cuda_check(cudaGetSymbolAddress(&a.prog, g_noalloc_prog), "cudaGetSymbolAddress(prog)");
+    cuda_check(cudaGetSymbolAddress(&a.ops, g_noalloc_ops), "cudaGetSymbolAddress(ops)");
+    cuda_check(cudaGetSymbolAddress(&a.consts, g_noalloc_consts), "cudaGetSymbolAddress(consts)");
+    a.ready = true;
+  }
+  return a;
+}
+
+template <typename Real>
+void launch_noalloc(const yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t st) {
+  // limits first: a request beyond the fixed arrays is an error, never a partial run
+  const size_t per_warp = (size_t)p->temp_entries * 32 * sizeof(Real);
+  const size_t slots = kNoAllocScratchBytes / per_warp;
+  YT_REQUIRE(slots >= 4, YT_ERR_UNSUPPORTED,
+             "plan temporaries need " + std::to_string(per_warp * 4) + " bytes per block; the "
+             "allocation-free scratch holds " + std::to_string(kNoAllocScratchBytes));
+  YT_REQUIRE(p->prog.size() <= kNoAllocProgInts, YT_ERR_UNSUPPORTED,
+             "plan index lists exceed the allocation-free limit of 2^20 integers");
+  YT_REQUIRE(p->ops.size() <= kNoAllocOps, YT_ERR_UNSUPPORTED,
+             "plan has more than 4096 operations");
+  std::vector<Real> consts;
+  for (size_t i = 0; i < p->tensors.size(); ++i)
+    if (p->tensors[i].global)
+      for (double v : p->tensors[i].values) consts.push_back((Real)v);
+  YT_REQUIRE(consts.size() * sizeof(Real) <= kNoAllocConstDoubles * sizeof(double), YT_ERR_UNSUPPORTED,
+             "plan constants exceed the allocation-free limit of 2 MiB");
+  ExecPtrs<Real> T{};
+  for (size_t i = 0; i < p->tensors.size(); ++i)
+    if (!p->tensors[i].global) {
+      YT_REQUIRE(ptrs[i] != nullptr, YT_ERR_INVALID, "null pointer for per-element tensor " + p->tensors[i].name);
+      T.p[p->slot_of_tensor[i]] = static_cast<Real*>(ptrs[i]);
+    }
+  int dev = 0, sms = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  const NoAllocAddrs a = noalloc_addrs(dev);
+  if (!p->prog.empty())
+    cuda_check(cudaMemcpyAsync(a.prog, p->prog.data(), p->prog.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy prog");
+  if (!p->ops.empty())
+    cuda_check(cudaMemcpyAsync(a.ops, p->ops.data(), p->ops.size() * sizeof(ExecOp), cudaMemcpyHostToDevice, st), "copy ops");
+  if (!consts.empty())
+    cuda_check(cudaMemcpyAsync(a.consts, consts.data(), consts.size() * sizeof(Real), cudaMemcpyHostToDevice, st), "copy consts");
+  const int64_t tiles = (n + 31) / 32;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>({(tiles + 3) / 4, (int64_t)sms * 8, (int64_t)(slots / 4)}));
+  k_execute<Real><<<(unsigned)blocks, 128, 0, st>>>(static_cast<const ExecOp*>(a.ops), (int)p->ops.size(),
+                                                      static_cast<const int*>(a.prog),
+                                                      static_cast<const Real*>(a.consts), T,
+                                                      static_cast<Real*>(a.scratch), p->temp_entries, n);
+  cuda_check(cudaGetLastError(), "k_execute launch");
+}
+
+}  // namespace
+
+extern "C" yt_status yt_execute_batched_noalloc(const yt_plan* p, void* const* element_tensors,
+                                                int64_t n_elements, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(p && element_tensors, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(n_elements >= 0, YT_ERR_INVALID, "negative element count");
+    if (n_elements == 0) return;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->prec == YT_F64) launch_noalloc<double>(p, element_tensors, n_elements, st);
+    else launch_noalloc<float>(p, element_tensors, n_elements, st);
+  });
+}
