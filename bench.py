@@ -40,7 +40,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"167e58dde606798c": {6: (336.535808e6 + 506.209792e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"a22a8529d82d5fcb": {6: (297.324800e6 + 746.231040e6) / 40000}}
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for rel in ("csrc/ader_kernels.cuh", "codegen.py"):
+        h.update(open(os.path.join(ROOT, "paper_1903_11521_gb300", rel), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -248,9 +255,9 @@ def run_ours(args):
     barrier()
     for k in range(K):
         ev[k][0].record(stream)
-        solver.step_local(stream=stream)
+        solver.step_phase(0, stream=stream)
         ev[k][1].record(stream)
-        solver.step_neighbour(stream=stream)
+        solver.step_phase(1, stream=stream)
         ev[k][2].record(stream)
     barrier()
     clk = clocks.stop()
@@ -305,7 +312,7 @@ def run_ours(args):
 
     flops_local = stats["local_flops"] * E
     achieved = flops_local / (local_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_local (derivatives + time integral + volume + local flux)",
+    roofline = {"bound": "alu", "kernel": "k_local (derivatives + time integral + volume + face projections + local flux products)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
@@ -315,8 +322,7 @@ def run_ours(args):
                 "flops_per_element": {"local": stats["local_flops"], "neighbour": stats["neighbour_flops"]}}
     # DRAM bytes per element of k_local from one ncu capture of a 40,000-tet case, valid
     # only for the kernel source it was taken on (scaled to E: traffic grows with E)
-    src = os.path.join(ROOT, "paper_1903_11521_gb300", "csrc", "ader_kernels.cuh")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_source_digest()
     if args.order in NCU_TRAFFIC_PER_ELEMENT.get(digest, {}):
         roofline["traffic"] = NCU_TRAFFIC_PER_ELEMENT[digest][args.order] * E
         roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, scaled)"

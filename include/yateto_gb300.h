@@ -199,11 +199,18 @@ yt_status yt_solver_get(struct yt_solver* solver, yt_field field, double* out,
 /* One full step: the local kernel (derivatives, time integral, volume, local flux),
  * then the neighbour kernel. */
 yt_status yt_step(struct yt_solver* solver, yt_stream stream);
-/* The two halves of yt_step, for partial updates and timing. */
+/* Partial updates: yt_step_local applies derivatives, time integral, volume and local
+ * flux (the complete local update); yt_step_neighbour then applies the neighbour flux.
+ * Together they give the same result as yt_step up to rounding. */
 yt_status yt_step_local(struct yt_solver* solver, yt_stream stream);
 yt_status yt_step_neighbour(struct yt_solver* solver, yt_stream stream);
-/* Non-zero flops per element of the local / neighbour kernels and their device bytes
- * per element (algorithmic: each stream read or written once). */
+/* The two kernels of yt_step, one at a time (phase 0 then phase 1 == yt_step): phase 0
+ * computes derivatives, time integral, volume, the face projections and the local flux
+ * products (R^sT I) Aloc_s^T; phase 1 adds the neighbour products and applies
+ * Rhat^s once per face to their sum.  Q is only consistent after phase 1. */
+yt_status yt_step_phase(struct yt_solver* solver, int32_t phase, yt_stream stream);
+/* Flops per element executed by the two phases of yt_step, and their algorithmic device
+ * bytes per element (each stream read or written once). */
 yt_status yt_solver_stats(const struct yt_solver* solver, double* local_flops,
                           double* neighbour_flops, double* local_bytes,
                           double* neighbour_bytes);

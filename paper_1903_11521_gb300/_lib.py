@@ -59,6 +59,7 @@ SIGNATURES = {
     "yt_step": (C.c_int, [_P, _P]),
     "yt_step_local": (C.c_int, [_P, _P]),
     "yt_step_neighbour": (C.c_int, [_P, _P]),
+    "yt_step_phase": (C.c_int, [_P, C.c_int32, _P]),
     "yt_solver_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "yt_solver_reference_matrix": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

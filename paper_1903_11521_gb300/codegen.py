@@ -1,0 +1,156 @@
+"""Build-time generator of the unrolled sparse loops of the ADER-DG kernels.
+
+For every polynomial degree N = 1..5 it emits ``_build/gen/yt_rows_o{N}.cuh`` with one
+specialisation ``Row<N, LIST, ROW>`` per row of every sparse list of the step (the CK
+derivative lists Ktilde^x restricted to the staircase, Khat^x, R^sT and Rhat^s): a
+straight-line sum over the row's non-zeros, values read at fixed offsets of the value
+array the solver uploads and operands at fixed offsets of the per-thread shared-memory
+column.  The sparsity patterns come from the library's own reference matrices (through a
+host-only helper library), and the value offsets follow the order in which the solver
+packs its CSR lists: derivative lists (delta, x), volume lists (x), then for every face
+R^sT and Rhat^s; rows in order, columns ascending.  ``ader_o{N}.cu`` instantiates the
+kernels of that degree in its own translation unit.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+ORDERS_N = (1, 2, 3, 4, 5)
+ROW_STRIDE = 9 * 32          # doubles between consecutive rows of a thread's column
+N_ACC = 4
+
+
+def host_helper(build_dir: str) -> str:
+    out = os.path.join(build_dir, "libyt_tables_host.so")
+    srcs = [os.path.join(CSRC, "tables.cpp"), os.path.join(CSRC, "host_tools", "tables_export.cpp")]
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(s) for s in
+                                                               srcs + [os.path.join(CSRC, "tables.h")]):
+        cxx = os.environ.get("CXX", "g++")
+        res = subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", *srcs, "-o", out],
+                             capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"host helper build failed:\n{res.stderr}")
+    return out
+
+
+def matrices(lib, N):
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    BT = (N + 1) * (N + 2) // 2
+
+    def get(name, count, shape):
+        buf = np.empty(count)
+        n = C.c_int64()
+        rc = lib.yt_host_reference_matrix(N, name.encode(), buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                          C.byref(n))
+        if rc != 0 or n.value != count:
+            raise RuntimeError(f"reference matrix {name} of degree {N}: status {rc}")
+        return buf.reshape(shape)        # stacked, each column-major: [.., col, row]
+
+    Kt = get("Ktilde", 3 * B * B, (3, B, B))
+    Kh = get("Khat", 3 * B * B, (3, B, B))
+    R = get("R", 4 * BT * B, (4, BT, B))
+    Rh = get("Rhat", 4 * BT * B, (4, BT, B))
+    return B, BT, Kt, Kh, R, Rh
+
+
+def lists(N, B, BT, Kt, Kh, R, Rh):
+    """[(list_id, rows)] in packing order; rows[r] = [(col, value_offset)]."""
+    nd = lambda d: (N - d + 3) * (N - d + 2) * (N - d + 1) // 6
+    out = []
+    off = 0
+
+    def add(list_id, nrows, ncols, at):
+        nonlocal off
+        rows = []
+        for r in range(nrows):
+            row = []
+            for c in range(ncols):
+                if at(r, c) != 0.0:
+                    row.append((c, off))
+                    off += 1
+            rows.append(row)
+        out.append((list_id, rows))
+
+    for d in range(N):
+        for x in range(3):
+            add(d * 3 + x, nd(d + 1), nd(d), lambda r, c, x=x: Kt[x][c, r])
+    for x in range(3):
+        add(18 + x, B, B, lambda r, c, x=x: Kh[x][c, r])
+    for f in range(4):
+        add(21 + f, BT, B, lambda r, c, f=f: R[f][r, c])       # R^sT: row m, column l
+        add(25 + f, B, BT, lambda r, c, f=f: Rh[f][c, r])      # Rhat^s: row k, column m
+    return out, off
+
+
+def emit_rows(N, lst):
+    lines = []
+    for list_id, rows in lst:
+        for r, row in enumerate(rows):
+            lines.append(f"template <> struct Row<{N}, {list_id}, {r}> {{")
+            lines.append("  static __device__ __forceinline__ double dot(const double* __restrict__ v, "
+                         "const double* __restrict__ x) {")
+            if not row:
+                lines.append("    return 0.0;")
+            else:
+                na = min(N_ACC, len(row))
+                for a in range(na):
+                    lines.append(f"    double a{a} = 0.0;")
+                for i, (c, voff) in enumerate(row):
+                    a = i % na
+                    lines.append(f"    a{a} = fma(__ldg(v + {voff}), x[{c * ROW_STRIDE}], a{a});")
+                terms = [f"a{a}" for a in range(na)]
+                while len(terms) > 1:
+                    terms = [f"({terms[i]} + {terms[i + 1]})" if i + 1 < len(terms) else terms[i]
+                             for i in range(0, len(terms), 2)]
+                lines.append(f"    return {terms[0]};")
+            lines.append("  }")
+            lines.append("};")
+    return "\n".join(lines) + "\n"
+
+
+UNIT = """// Generated by codegen.py: kernels of polynomial degree {N}.
+#include "ader_kernels.cuh"
+#include "yt_rows_o{N}.cuh"
+
+namespace yt {{
+void ader_set_attributes_o{N}(size_t smem_local, size_t smem_neigh) {{
+  ader_set_attributes<{N}>(smem_local, smem_neigh);
+}}
+void ader_launch_local_o{N}(const AderLaunch& L, bool fused) {{ ader_launch_local<{N}>(L, fused); }}
+void ader_launch_neigh_o{N}(const AderLaunch& L, bool fused) {{ ader_launch_neigh<{N}>(L, fused); }}
+int ader_generated_nnz_o{N}() {{ return {NVALS}; }}
+}}  // namespace yt
+"""
+
+
+def generate(build_dir: str) -> list[str]:
+    gen = os.path.join(build_dir, "gen")
+    os.makedirs(gen, exist_ok=True)
+    lib = C.CDLL(host_helper(build_dir))
+    lib.yt_host_reference_matrix.restype = C.c_int
+    lib.yt_host_reference_matrix.argtypes = [C.c_int, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    units = []
+    for N in ORDERS_N:
+        B, BT, Kt, Kh, R, Rh = matrices(lib, N)
+        lst, nvals = lists(N, B, BT, Kt, Kh, R, Rh)
+        header = (f"// Generated by codegen.py: unrolled sparse rows of polynomial degree {N} "
+                  f"({nvals} non-zeros).\n#pragma once\nnamespace yt {{\nnamespace gen {{\n"
+                  + emit_rows(N, lst) + "}  // namespace gen\n}  // namespace yt\n")
+        _write_if_changed(os.path.join(gen, f"yt_rows_o{N}.cuh"), header)
+        unit = os.path.join(gen, f"ader_o{N}.cu")
+        _write_if_changed(unit, UNIT.format(N=N, NVALS=nvals))
+        units.append(unit)
+    return units
+
+
+def _write_if_changed(path, text):
+    if os.path.exists(path) and open(path).read() == text:
+        return
+    with open(path, "w") as f:
+        f.write(text)

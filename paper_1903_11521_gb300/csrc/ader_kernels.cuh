@@ -13,8 +13,11 @@
 // [tile][...entries...][32 lanes], so a warp's access to one entry of 32 elements is one
 // contiguous 256-byte segment.
 //
-// The global matrices are stored as CSR lists of their non-zeros (structural zeros and
-// the equivalent-sparsity zero blocks of Sec. 4.2 / 5.1.2 are never multiplied):
+// Sparse products with the global matrices are straight-line code generated per degree
+// (codegen.py): every non-zero of the list is one fma with its value read at a fixed
+// offset of the solver's value array and its operand at a fixed shared-memory offset, so
+// structural zeros and the equivalent-sparsity zero blocks (Sec. 4.2, 5.1.2) are never
+// multiplied:
 //   CK derivative delta: Ktilde^x restricted to rows < C(N-delta+2,3), columns
 //                        < C(N-delta+3,3) (the derivative staircase);
 //   volume:              Khat^x (zero columns l >= C(N+2,3) are absent);
@@ -25,7 +28,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace yt {
+
+namespace gen {
+// Row<N, LIST, ROW>::dot(v, x) = sum over the non-zeros (l, value offset o) of row ROW of
+// sparse list LIST of v[o] * x[l * 9 * 32]; specialisations are generated per degree N
+// (codegen.py) with every non-zero unrolled.  Lists: 3*delta + x = derivative delta,
+// direction x; 18 + x = volume Khat^x; 21 + s = R^sT; 25 + s = Rhat^s.
+template <int N, int LIST, int ROW>
+struct Row;
+}  // namespace gen
+
+template <int Begin, int End, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (Begin < End) {
+    f(std::integral_constant<int, Begin>{});
+    static_for<Begin + 1, End>(f);
+  }
+}
 
 constexpr int kTile = 32;
 constexpr int kNq = 9;
@@ -63,24 +85,6 @@ struct StepTables {
   double coeff[8];      // dt^{d+1} / (d+1)!
 };
 
-// ---------------------------------------------------------------- sparse row helper
-// acc = sum over the non-zeros (l, v) of row `row` of one CSR list of v * X[l][w][lane].
-__device__ __forceinline__ double csr_row_dot(const StepTables& T, int off, int row,
-                                              const double* __restrict__ X, int w, int lane) {
-  const int b = __ldg(T.rp + off + row);
-  const int e = __ldg(T.rp + off + row + 1);
-  double a0 = 0.0, a1 = 0.0;
-  int i = b;
-  for (; i + 1 < e; i += 2) {
-    const int c0 = __ldg(T.col + i), c1 = __ldg(T.col + i + 1);
-    const double v0 = __ldg(T.val + i), v1 = __ldg(T.val + i + 1);
-    a0 = fma(v0, X[(c0 * kNq + w) * kTile + lane], a0);
-    a1 = fma(v1, X[(c1 * kNq + w) * kTile + lane], a1);
-  }
-  if (i < e) a0 = fma(__ldg(T.val + i), X[(__ldg(T.col + i) * kNq + w) * kTile + lane], a0);
-  return a0 + a1;
-}
-
 // ------------------------------------------------------------------- CK derivatives
 // One derivative step delta -> delta+1, in place in Dsh (see the degree argument in the
 // solver's design notes: output row k only reads rows of higher polynomial degree, which
@@ -94,23 +98,23 @@ __device__ __forceinline__ void ck_step(const StepTables& T, const int (&scol)[3
   if constexpr (DELTA < N) {
     constexpr int nout = Dm::nd(DELTA + 1);
     constexpr int KC = Dm::KC;
-#pragma unroll
-    for (int k0 = 0; k0 < nout; k0 += KC) {
+    const double* xcol = Dsh + w * kTile + lane;
+    static_for<0, (nout + KC - 1) / KC>([&](auto chunk) {
+      constexpr int k0 = decltype(chunk)::value * KC;
       // X^x[k][q] = sum_l Ktilde^x_kl D[l][q]  (this thread: column q = w)
-#pragma unroll
-      for (int kk = 0; kk < KC; ++kk) {
-        if (k0 + kk < nout) {
-#pragma unroll
-          for (int x = 0; x < 3; ++x)
-            Xsh[((x * KC + kk) * kNq + w) * kTile + lane] =
-                csr_row_dot(T, T.ck[DELTA][x], k0 + kk, Dsh, w, lane);
+      static_for<0, KC>([&](auto kkc) {
+        constexpr int kk = decltype(kkc)::value;
+        if constexpr (k0 + kk < nout) {
+          Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 0, k0 + kk>::dot(T.val, xcol);
+          Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 1, k0 + kk>::dot(T.val, xcol);
+          Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 2, k0 + kk>::dot(T.val, xcol);
         }
-      }
+      });
       __syncthreads();
       // D^{delta+1}[k][p] = sum_x sum_q Astar^x_pq X^x[k][q]  (this thread: row p = w)
-#pragma unroll
-      for (int kk = 0; kk < KC; ++kk) {
-        if (k0 + kk < nout) {
+      static_for<0, KC>([&](auto kkc) {
+        constexpr int kk = decltype(kkc)::value;
+        if constexpr (k0 + kk < nout) {
           double v = 0.0;
 #pragma unroll
           for (int x = 0; x < 3; ++x)
@@ -120,9 +124,9 @@ __device__ __forceinline__ void ck_step(const StepTables& T, const int (&scol)[3
           Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
           Icol[k0 + kk] = fma(T.coeff[DELTA + 1], v, Icol[k0 + kk]);
         }
-      }
+      });
       __syncthreads();
-    }
+    });
     ck_step<N, DELTA + 1>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
   }
 }
@@ -134,10 +138,14 @@ __device__ __forceinline__ void ck_step(const StepTables& T, const int (&scol)[3
 //   Pface   : [tile][4][9][BT][32]   projections R^sT I of the four faces
 //   star    : [tile][3][24][32]      non-zero slots of Astar^x
 //   floc    : [tile][4][9][9][32]    local flux solvers (row p, column q)
-template <int N>
+//   Wloc    : [tile][4][9][BT][32]   (R^sT I) Aloc_s^T per face, written when LIFT is
+//                                    false (the full step lifts it together with the
+//                                    neighbour contribution in k_neigh)
+// LIFT = true applies the local flux here (Q is then the complete local update).
+template <int N, bool LIFT>
 __global__ void __launch_bounds__(kNq * kTile, 1)
 k_local(const double* Q, double* Qout, double* __restrict__ Iout,
-        double* __restrict__ Pface, const double* __restrict__ star,
+        double* __restrict__ Pface, double* __restrict__ Wloc, const double* __restrict__ star,
         const double* __restrict__ floc, StepTables T, StarPattern SP) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
@@ -179,46 +187,53 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
     It[(w * B + k) * kTile + lane] = Icol[k];
   }
 
-  double dQ[B];
-#pragma unroll
-  for (int k = 0; k < B; ++k) dQ[k] = 0.0;
+  // With LIFT the local flux is added to every row after the volume term, so the update
+  // is accumulated in registers; without it the volume term completes each row of Q,
+  // which is written as soon as its chunk is done.
+  double dQ[LIFT ? B : 1];
+  double* Qo = Qout + tile * (kNq * B * kTile);
 
   // volume: dQ[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q]
-#pragma unroll
-  for (int k0 = 0; k0 < B; k0 += KC) {
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk)
-      if (k0 + kk < B) {
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-          Xsh[((x * KC + kk) * kNq + w) * kTile + lane] = csr_row_dot(T, T.vol[x], k0 + kk, Dsh, w, lane);
+  const double* icol = Dsh + w * kTile + lane;
+  static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
+    constexpr int k0 = decltype(chunk)::value * KC;
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      if constexpr (k0 + kk < B) {
+        Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 18, k0 + kk>::dot(T.val, icol);
+        Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 19, k0 + kk>::dot(T.val, icol);
+        Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 20, k0 + kk>::dot(T.val, icol);
       }
+    });
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk)
-      if (k0 + kk < B) {
-        double v = dQ[k0 + kk];
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      if constexpr (k0 + kk < B) {
+        constexpr int k = k0 + kk;
+        double v = 0.0;
 #pragma unroll
         for (int x = 0; x < 3; ++x)
 #pragma unroll
           for (int s = 0; s < 3; ++s)
             if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-        dQ[k0 + kk] = v;
+        if constexpr (LIFT) dQ[k] = v;
+        else Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + v;
       }
+    });
     __syncthreads();
-  }
+  });
 
   // local flux: dQ += Rhat^s ((R^sT I) Aloc_s^T)
   double* Pt = Pface + tile * (4 * kNq * BT * kTile);
   const double* Ft = floc + tile * (4 * kNq * kNq * kTile);
-#pragma unroll 1
-  for (int s = 0; s < 4; ++s) {
-#pragma unroll
-    for (int m = 0; m < BT; ++m) {
-      const double z = csr_row_dot(T, T.rT[s], m, Dsh, w, lane);
+  static_for<0, 4>([&](auto face) {
+    constexpr int s = decltype(face)::value;
+    static_for<0, BT>([&](auto mm) {
+      constexpr int m = decltype(mm)::value;
+      const double z = gen::Row<N, 21 + s, m>::dot(T.val, icol);
       Xsh[(m * kNq + w) * kTile + lane] = z;
       Pt[((s * kNq + w) * BT + m) * kTile + lane] = z;
-    }
+    });
     double a[kNq];
 #pragma unroll
     for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
@@ -232,25 +247,37 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
       Wr[m] = v;
     }
     __syncthreads();
+    if constexpr (LIFT) {
 #pragma unroll
-    for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
+      for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
+      const double* wcol = Xsh + w * kTile + lane;
+      static_for<0, B>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        dQ[k] += gen::Row<N, 25 + s, k>::dot(T.val, wcol);
+      });
+    } else {
+      double* Wt = Wloc + tile * (4 * kNq * BT * kTile);
 #pragma unroll
-    for (int k = 0; k < B; ++k) dQ[k] += csr_row_dot(T, T.rhat[s], k, Xsh, w, lane);
-  }
+      for (int m = 0; m < BT; ++m) Wt[((s * kNq + w) * BT + m) * kTile + lane] = Wr[m];
+    }
+  });
 
-  double* Qo = Qout + tile * (kNq * B * kTile);
+  if constexpr (LIFT) {
 #pragma unroll
-  for (int k = 0; k < B; ++k) Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + dQ[k];
+    for (int k = 0; k < B; ++k) Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + dQ[k];
+  }
 }
 
 // ------------------------------------------------------------------------- K_neigh
 // Neighbour flux of one tile: dQ += Rhat^s f^h (R^jT I_nb) Anb_s^T, with R^jT I_nb read
 // from the neighbour's face projections written by k_local.
 //   conn : [E_pad][4] packed (neighbour << 4) | (j << 2) | h
-template <int N>
+// WITH_LOCAL: add the local flux terms Wloc written by k_local<N, false> before lifting,
+// so that Rhat^s is applied once per face to the sum of both flux contributions.
+template <int N, bool WITH_LOCAL>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ fnb,
-        const int* __restrict__ conn, StepTables T) {
+k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ Wloc,
+        const double* __restrict__ fnb, const int* __restrict__ conn, StepTables T) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT;
   extern __shared__ double smem[];
@@ -265,8 +292,8 @@ k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ 
   for (int k = 0; k < B; ++k) dQ[k] = 0.0;
   const double* Ft = fnb + tile * (4 * kNq * kNq * kTile);
 
-#pragma unroll 1
-  for (int s = 0; s < 4; ++s) {
+  static_for<0, 4>([&](auto face) {
+    constexpr int s = decltype(face)::value;
     const int c = __ldg(conn + e * 4 + s);
     const size_t nb = (size_t)(c >> 4);
     const int j = (c >> 2) & 3, h = c & 3;
@@ -295,6 +322,7 @@ k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ 
 #pragma unroll
     for (int m = 0; m < BT; ++m) {
       double v = 0.0;
+      if constexpr (WITH_LOCAL) v = __ldg(Wloc + ((tile * 4 + s) * kNq * BT + w * BT + m) * kTile + lane);
 #pragma unroll
       for (int q = 0; q < kNq; ++q) v = fma(a[q], Xsh[(m * kNq + q) * kTile + lane], v);
       Wr[m] = v;
@@ -302,12 +330,80 @@ k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
-#pragma unroll
-    for (int k = 0; k < B; ++k) dQ[k] += csr_row_dot(T, T.rhat[s], k, Xsh, w, lane);
-  }
+    const double* wcol = Xsh + w * kTile + lane;
+    static_for<0, B>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      dQ[k] += gen::Row<N, 25 + s, k>::dot(T.val, wcol);
+    });
+  });
   double* Qt = Q + tile * (kNq * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) Qt[(w * B + k) * kTile + lane] += dQ[k];
 }
+
+// ------------------------------------------------------------------ launch helpers
+struct AderLaunch {
+  int64_t ntiles;
+  size_t smem_local, smem_neigh;
+  double *Q, *I, *Pface, *Wloc;
+  const double *star, *floc, *fnb;
+  const int* conn;
+  StepTables T;
+  StarPattern SP;
+  cudaStream_t stream;
+};
+
+template <int N>
+void ader_set_attributes(size_t smem_local, size_t smem_neigh) {
+  cudaFuncSetAttribute(k_local<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_local);
+  cudaFuncSetAttribute(k_local<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_local);
+  cudaFuncSetAttribute(k_neigh<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_neigh);
+  cudaFuncSetAttribute(k_neigh<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_neigh);
+}
+
+// fused = true: the local half of the full step (local flux lifted in k_neigh)
+template <int N>
+void ader_launch_local(const AderLaunch& L, bool fused) {
+  const unsigned grid = (unsigned)L.ntiles;
+  if (fused)
+    k_local<N, false><<<grid, kNq * kTile, L.smem_local, L.stream>>>(L.Q, L.Q, L.I, L.Pface, L.Wloc,
+                                                                       L.star, L.floc, L.T, L.SP);
+  else
+    k_local<N, true><<<grid, kNq * kTile, L.smem_local, L.stream>>>(L.Q, L.Q, L.I, L.Pface, L.Wloc,
+                                                                      L.star, L.floc, L.T, L.SP);
+}
+
+template <int N>
+void ader_launch_neigh(const AderLaunch& L, bool fused) {
+  const unsigned grid = (unsigned)L.ntiles;
+  if (fused)
+    k_neigh<N, true><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(L.Q, L.Pface, L.Wloc, L.fnb,
+                                                                      L.conn, L.T);
+  else
+    k_neigh<N, false><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(L.Q, L.Pface, L.Wloc, L.fnb,
+                                                                       L.conn, L.T);
+}
+
+// per-degree instantiations live in generated translation units
+void ader_set_attributes_o1(size_t, size_t);
+void ader_set_attributes_o2(size_t, size_t);
+void ader_set_attributes_o3(size_t, size_t);
+void ader_set_attributes_o4(size_t, size_t);
+void ader_set_attributes_o5(size_t, size_t);
+void ader_launch_local_o1(const AderLaunch&, bool);
+void ader_launch_local_o2(const AderLaunch&, bool);
+void ader_launch_local_o3(const AderLaunch&, bool);
+void ader_launch_local_o4(const AderLaunch&, bool);
+void ader_launch_local_o5(const AderLaunch&, bool);
+void ader_launch_neigh_o1(const AderLaunch&, bool);
+void ader_launch_neigh_o2(const AderLaunch&, bool);
+void ader_launch_neigh_o3(const AderLaunch&, bool);
+void ader_launch_neigh_o4(const AderLaunch&, bool);
+void ader_launch_neigh_o5(const AderLaunch&, bool);
+int ader_generated_nnz_o1();
+int ader_generated_nnz_o2();
+int ader_generated_nnz_o3();
+int ader_generated_nnz_o4();
+int ader_generated_nnz_o5();
 
 }  // namespace yt

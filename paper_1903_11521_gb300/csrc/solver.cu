@@ -186,8 +186,8 @@ struct yt_solver {
   yt_precision prec = YT_F64;
   double dt = 0.0;
   bool has_neighbours = false;
-  double *Q = nullptr, *I = nullptr, *Pface = nullptr, *star = nullptr, *floc = nullptr,
-         *fnb = nullptr, *staging = nullptr;
+  double *Q = nullptr, *I = nullptr, *Pface = nullptr, *Wloc = nullptr, *star = nullptr,
+         *floc = nullptr, *fnb = nullptr, *staging = nullptr;
   int* conn = nullptr;
   int* d_rp = nullptr;
   uint16_t* d_col = nullptr;
@@ -195,9 +195,11 @@ struct yt_solver {
   double* d_f = nullptr;
   StepTables T{};
   double flops_local = 0, flops_neigh = 0, bytes_local = 0, bytes_neigh = 0;
+  double flops_local_unfused = 0;
+  int64_t n_values = 0;
   size_t smem_local = 0, smem_neigh = 0;
   ~yt_solver() {
-    for (void* p : {(void*)Q, (void*)I, (void*)Pface, (void*)star, (void*)floc, (void*)fnb,
+    for (void* p : {(void*)Q, (void*)I, (void*)Pface, (void*)Wloc, (void*)star, (void*)floc, (void*)fnb,
                     (void*)staging, (void*)conn, (void*)d_rp, (void*)d_col, (void*)d_val,
                     (void*)d_f})
       if (p) cudaFree(p);
@@ -206,56 +208,76 @@ struct yt_solver {
 
 namespace {
 
-template <int N>
-void set_smem_attrs(yt_solver* s) {
-  using Dm = Dims<N>;
-  s->smem_local = sizeof(double) * (Dm::B + Dm::XR) * kNq * kTile;
-  s->smem_neigh = sizeof(double) * Dm::BT * kNq * kTile;
-  cuda_check(cudaFuncSetAttribute(k_local<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)s->smem_local), "cudaFuncSetAttribute(k_local)");
-  cuda_check(cudaFuncSetAttribute(k_neigh<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)s->smem_neigh), "cudaFuncSetAttribute(k_neigh)");
+AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
+  AderLaunch L;
+  L.ntiles = s->ntiles;
+  L.smem_local = s->smem_local;
+  L.smem_neigh = s->smem_neigh;
+  L.Q = s->Q;
+  L.I = s->I;
+  L.Pface = s->Pface;
+  L.Wloc = s->Wloc;
+  L.star = s->star;
+  L.floc = s->floc;
+  L.fnb = s->fnb;
+  L.conn = s->conn;
+  L.T = s->T;
+  L.SP = kStar;
+  L.stream = st;
+  return L;
 }
 
-template <int N>
-void launch_local(yt_solver* s, cudaStream_t st) {
-  k_local<N><<<(unsigned)s->ntiles, kNq * kTile, s->smem_local, st>>>(
-      s->Q, s->Q, s->I, s->Pface, s->star, s->floc, s->T, kStar);
-}
-template <int N>
-void launch_neigh(yt_solver* s, cudaStream_t st) {
-  k_neigh<N><<<(unsigned)s->ntiles, kNq * kTile, s->smem_neigh, st>>>(s->Q, s->Pface, s->fnb,
-                                                                      s->conn, s->T);
-}
-
-void dispatch_smem(yt_solver* s) {
-  switch (s->N) {
-    case 1: set_smem_attrs<1>(s); break;
-    case 2: set_smem_attrs<2>(s); break;
-    case 3: set_smem_attrs<3>(s); break;
-    case 4: set_smem_attrs<4>(s); break;
-    case 5: set_smem_attrs<5>(s); break;
+// Shared memory of the two kernels of degree N (FP64): k_local holds the B-row column
+// buffer and the exchange buffer, k_neigh the exchange buffer only.
+void set_smem(yt_solver* s) {
+  const int N = s->N;
+  const int B = n_basis(N), BT = n_face_basis(N);
+  const int KC = BT / 3 > 0 ? BT / 3 : 1;
+  const int XR = 3 * KC > BT ? 3 * KC : BT;
+  s->smem_local = sizeof(double) * (size_t)(B + XR) * kNq * kTile;
+  s->smem_neigh = sizeof(double) * (size_t)BT * kNq * kTile;
+  switch (N) {
+    case 1: ader_set_attributes_o1(s->smem_local, s->smem_neigh); break;
+    case 2: ader_set_attributes_o2(s->smem_local, s->smem_neigh); break;
+    case 3: ader_set_attributes_o3(s->smem_local, s->smem_neigh); break;
+    case 4: ader_set_attributes_o4(s->smem_local, s->smem_neigh); break;
+    case 5: ader_set_attributes_o5(s->smem_local, s->smem_neigh); break;
     default: throw Error(YT_ERR_UNSUPPORTED, "FP64 solver supports orders 2..6");
   }
+  cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
 }
-void dispatch_local(yt_solver* s, cudaStream_t st) {
+
+int generated_nnz(int N) {
+  switch (N) {
+    case 1: return ader_generated_nnz_o1();
+    case 2: return ader_generated_nnz_o2();
+    case 3: return ader_generated_nnz_o3();
+    case 4: return ader_generated_nnz_o4();
+    case 5: return ader_generated_nnz_o5();
+  }
+  return -1;
+}
+
+void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
+  const AderLaunch L = launch_args(s, st);
   switch (s->N) {
-    case 1: launch_local<1>(s, st); break;
-    case 2: launch_local<2>(s, st); break;
-    case 3: launch_local<3>(s, st); break;
-    case 4: launch_local<4>(s, st); break;
-    case 5: launch_local<5>(s, st); break;
+    case 1: ader_launch_local_o1(L, fused); break;
+    case 2: ader_launch_local_o2(L, fused); break;
+    case 3: ader_launch_local_o3(L, fused); break;
+    case 4: ader_launch_local_o4(L, fused); break;
+    case 5: ader_launch_local_o5(L, fused); break;
     default: throw Error(YT_ERR_UNSUPPORTED, "order");
   }
   cuda_check(cudaGetLastError(), "k_local launch");
 }
-void dispatch_neigh(yt_solver* s, cudaStream_t st) {
+void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
+  const AderLaunch L = launch_args(s, st);
   switch (s->N) {
-    case 1: launch_neigh<1>(s, st); break;
-    case 2: launch_neigh<2>(s, st); break;
-    case 3: launch_neigh<3>(s, st); break;
-    case 4: launch_neigh<4>(s, st); break;
-    case 5: launch_neigh<5>(s, st); break;
+    case 1: ader_launch_neigh_o1(L, fused); break;
+    case 2: ader_launch_neigh_o2(L, fused); break;
+    case 3: ader_launch_neigh_o3(L, fused); break;
+    case 4: ader_launch_neigh_o4(L, fused); break;
+    case 5: ader_launch_neigh_o5(L, fused); break;
     default: throw Error(YT_ERR_UNSUPPORTED, "order");
   }
   cuda_check(cudaGetLastError(), "k_neigh launch");
@@ -283,7 +305,7 @@ void build_tables(yt_solver* s) {
     for (int r = 0; r < B; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.vol[x], r) + 1.0);
   }
   fl += B * 2.0 * 3 * kStarSlots;
-  double fn = 0.0;
+  double fn = 0.0, lift_total = 0.0;
   for (int f = 0; f < 4; ++f) {
     const double* Rs = R.R.data() + (size_t)f * B * BT;
     const double* Rh = R.Rhat.data() + (size_t)f * B * BT;
@@ -292,19 +314,24 @@ void build_tables(yt_solver* s) {
     double lift = 0.0;
     for (int r = 0; r < BT; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.rT[f], r) + 1.0);
     for (int r = 0; r < B; ++r) lift += 9.0 * (2.0 * csr.row_nnz(s->T.rhat[f], r) + 1.0 + 1.0);
-    fl += BT * 2.0 * 81 + lift;
+    fl += BT * 2.0 * 81;
+    lift_total += lift;
     double blocks = 0.0;
     for (int d = 0; d <= N; ++d) blocks += (d + 1.0) * (d + 1.0);
     fn += 9.0 * 2.0 * blocks + BT * 2.0 * 81 + lift;
   }
   fl += 9.0 * B;                                           // Q + dQ
   fn += 9.0 * B;
+  // yt_step runs k_local without the local lifting and k_neigh with the local products
+  // added (one addition per entry of W) before the single lifting
   s->flops_local = fl;
-  s->flops_neigh = fn;
+  s->flops_neigh = fn + 4.0 * 9 * BT;
+  s->flops_local_unfused = fl + lift_total;
   const double qb = 8.0 * 9 * B, pb = 8.0 * 4 * 9 * BT;
-  s->bytes_local = 3 * qb + pb + 8.0 * (3 * kStarSlots + 4 * 81);
-  s->bytes_neigh = 2 * qb + pb + 8.0 * 4 * 81 + 16.0;
+  s->bytes_local = 3 * qb + 2 * pb + 8.0 * (3 * kStarSlots + 4 * 81);   // + Wloc written
+  s->bytes_neigh = 2 * qb + 2 * pb + 8.0 * 4 * 81 + 16.0;               // + Wloc read
   if (csr.col.size() > 0x7fffffff) throw Error(YT_ERR_UNSUPPORTED, "tables too large");
+  s->n_values = (int64_t)csr.val.size();
   s->d_rp = dalloc<int>(csr.rp.size());
   s->d_col = dalloc<uint16_t>(csr.col.size());
   s->d_val = dalloc<double>(csr.val.size());
@@ -366,12 +393,15 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
         }
     }
     build_tables(s.get());
-    dispatch_smem(s.get());
+    YT_REQUIRE(generated_nnz(s->N) == (int)s->n_values, YT_ERR_INVALID,
+               "generated kernels do not match the reference matrices (rebuild the library)");
+    set_smem(s.get());
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t nq = (size_t)s->Epad * kNq * s->B;
     s->Q = dalloc<double>(nq);
     s->I = dalloc<double>(nq);
     s->Pface = dalloc<double>((size_t)s->Epad * 4 * kNq * s->BT);
+    s->Wloc = dalloc<double>((size_t)s->Epad * 4 * kNq * s->BT);
     s->star = dalloc<double>((size_t)s->Epad * 3 * kStarSlots);
     s->floc = dalloc<double>((size_t)s->Epad * 4 * 81);
     s->fnb = dalloc<double>((size_t)s->Epad * 4 * 81);
@@ -443,7 +473,7 @@ extern "C" yt_status yt_solver_get(yt_solver* s, yt_field field, double* out, yt
 extern "C" yt_status yt_step_local(yt_solver* s, yt_stream stream) {
   return guarded([&] {
     YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
-    dispatch_local(s, reinterpret_cast<cudaStream_t>(stream));
+    dispatch_local(s, reinterpret_cast<cudaStream_t>(stream), false);
   });
 }
 
@@ -451,7 +481,18 @@ extern "C" yt_status yt_step_neighbour(yt_solver* s, yt_stream stream) {
   return guarded([&] {
     YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
     YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
-    dispatch_neigh(s, reinterpret_cast<cudaStream_t>(stream));
+    dispatch_neigh(s, reinterpret_cast<cudaStream_t>(stream), false);
+  });
+}
+
+extern "C" yt_status yt_step_phase(yt_solver* s, int32_t phase, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(phase == 0 || phase == 1, YT_ERR_INVALID, "phase must be 0 or 1");
+    YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (phase == 0) dispatch_local(s, st, true);
+    else dispatch_neigh(s, st, true);
   });
 }
 
@@ -460,8 +501,8 @@ extern "C" yt_status yt_step(yt_solver* s, yt_stream stream) {
     YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
     YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    dispatch_local(s, st);
-    dispatch_neigh(s, st);
+    dispatch_local(s, st, true);
+    dispatch_neigh(s, st, true);
   });
 }
 

@@ -104,6 +104,9 @@ class Solver:
         _lib.check(self.lib.yt_step_neighbour(self.handle, _stream_handle(stream)),
                    "yt_step_neighbour")
 
+    def step_phase(self, phase: int, stream=None):
+        _lib.check(self.lib.yt_step_phase(self.handle, phase, _stream_handle(stream)), "yt_step_phase")
+
     def stats(self):
         v = [C.c_double() for _ in range(4)]
         _lib.check(self.lib.yt_solver_stats(self.handle, *[C.byref(x) for x in v]),

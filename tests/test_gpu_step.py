@@ -123,3 +123,26 @@ def test_deterministic(yt):
     a, _ = run_gpu(yt, el, conn, Q, dt, 5)
     b, _ = run_gpu(yt, el, conn, Q, dt, 5)
     assert np.array_equal(a, b)
+
+
+def test_phases_equal_step_and_unfused_path(yt):
+    """yt_step == phase 0 + phase 1 (bitwise); the unfused pair yt_step_local +
+    yt_step_neighbour agrees within the FP64 tolerance."""
+    el, conn, Q, dt = make_case(96, 6, "impedance", seed=21)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    outs = []
+    for mode in ("step", "phases", "unfused"):
+        s = yt.Solver(6, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient)
+        s.set_dofs_host(Q)
+        if mode == "step":
+            s.step()
+        elif mode == "phases":
+            s.step_phase(0)
+            s.step_phase(1)
+        else:
+            s.step_local()
+            s.step_neighbour()
+        outs.append(s.get_host())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert rel_per_quantity(outs[2], outs[0]).max() < TOL
