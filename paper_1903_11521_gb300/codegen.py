@@ -8,8 +8,9 @@ array the solver uploads and operands at fixed offsets of the per-thread shared-
 column.  The sparsity patterns come from the library's own reference matrices (through a
 host-only helper library), and the value offsets follow the order in which the solver
 packs its CSR lists: derivative lists (delta, x), volume lists (x), then for every face
-R^sT and Rhat^s; rows in order, columns ascending.  ``ader_o{N}.cu`` instantiates the
-kernels of that degree in its own translation unit.
+R^sT and Rhat^s; rows in order, columns ascending.  ``ader_o{N}_{prec}_{variant}.cu`` instantiates
+one kernel variant of that degree and precision in its own translation unit, so that the
+units compile in parallel.
 """
 from __future__ import annotations
 
@@ -21,7 +22,10 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-ORDERS_N = (1, 2, 3, 4, 5)
+ORDERS_N = (1, 2, 3, 4, 5, 6)
+# (degree, contraction type) pairs that get kernels; degree 6 in FP64 does not fit the
+# shared memory of one CTA
+UNITS = [(n, "f64") for n in (1, 2, 3, 4, 5)] + [(n, "f32") for n in (1, 2, 3, 4, 5, 6)]
 ROW_STRIDE = 9 * 32          # doubles between consecutive rows of a thread's column
 N_ACC = 4
 
@@ -93,14 +97,15 @@ def emit_rows(N, lst):
     for list_id, rows in lst:
         for r, row in enumerate(rows):
             lines.append(f"template <> struct Row<{N}, {list_id}, {r}> {{")
-            lines.append("  static __device__ __forceinline__ double dot(const double* __restrict__ v, "
-                         "const double* __restrict__ x) {")
+            lines.append("  template <typename R>")
+            lines.append("  static __device__ __forceinline__ R dot(const R* __restrict__ v, "
+                         "const R* __restrict__ x) {")
             if not row:
-                lines.append("    return 0.0;")
+                lines.append("    return R(0);")
             else:
                 na = min(N_ACC, len(row))
                 for a in range(na):
-                    lines.append(f"    double a{a} = 0.0;")
+                    lines.append(f"    R a{a} = R(0);")
                 for i, (c, voff) in enumerate(row):
                     a = i % na
                     lines.append(f"    a{a} = fma(__ldg(v + {voff}), x[{c * ROW_STRIDE}], a{a});")
@@ -114,17 +119,29 @@ def emit_rows(N, lst):
     return "\n".join(lines) + "\n"
 
 
-UNIT = """// Generated by codegen.py: kernels of polynomial degree {N}.
+VARIANTS = {"lf": ("true", "true"), "ll": ("true", "false"), "nf": ("false", "true"),
+            "np": ("false", "false")}
+
+UNIT = """// Generated by codegen.py: one kernel variant ({V}) of polynomial degree {N},
+// contraction type {REAL}.
 #include "ader_kernels.cuh"
 #include "yt_rows_o{N}.cuh"
 
 namespace yt {{
-void ader_set_attributes_o{N}(size_t smem_local, size_t smem_neigh) {{
-  ader_set_attributes<{N}>(smem_local, smem_neigh);
+void ader_set_attribute_o{N}_{P}_{V}(size_t smem) {{ ader_set_attribute<{N}, {REAL}, {LOCAL}, {FUSED}>(smem); }}
+void ader_launch_o{N}_{P}_{V}(const AderLaunch& L) {{ ader_launch<{N}, {REAL}, {LOCAL}, {FUSED}>(L); }}
+}}  // namespace yt
+"""
+
+INFO = """// Generated by codegen.py: number of packed non-zero values per degree, checked by the
+// solver against its own packing of the reference matrices.
+namespace yt {{
+int ader_generated_nnz(int N) {{
+  switch (N) {{
+{CASES}
+  }}
+  return -1;
 }}
-void ader_launch_local_o{N}(const AderLaunch& L, bool fused) {{ ader_launch_local<{N}>(L, fused); }}
-void ader_launch_neigh_o{N}(const AderLaunch& L, bool fused) {{ ader_launch_neigh<{N}>(L, fused); }}
-int ader_generated_nnz_o{N}() {{ return {NVALS}; }}
 }}  // namespace yt
 """
 
@@ -136,16 +153,25 @@ def generate(build_dir: str) -> list[str]:
     lib.yt_host_reference_matrix.restype = C.c_int
     lib.yt_host_reference_matrix.argtypes = [C.c_int, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     units = []
+    counts = {}
     for N in ORDERS_N:
         B, BT, Kt, Kh, R, Rh = matrices(lib, N)
         lst, nvals = lists(N, B, BT, Kt, Kh, R, Rh)
+        counts[N] = nvals
         header = (f"// Generated by codegen.py: unrolled sparse rows of polynomial degree {N} "
                   f"({nvals} non-zeros).\n#pragma once\nnamespace yt {{\nnamespace gen {{\n"
                   + emit_rows(N, lst) + "}  // namespace gen\n}  // namespace yt\n")
         _write_if_changed(os.path.join(gen, f"yt_rows_o{N}.cuh"), header)
-        unit = os.path.join(gen, f"ader_o{N}.cu")
-        _write_if_changed(unit, UNIT.format(N=N, NVALS=nvals))
-        units.append(unit)
+    for N, P in UNITS:
+        for V, (local, fused) in VARIANTS.items():
+            unit = os.path.join(gen, f"ader_o{N}_{P}_{V}.cu")
+            _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused,
+                                                REAL="double" if P == "f64" else "float"))
+            units.append(unit)
+    info = os.path.join(gen, "ader_gen_info.cu")
+    cases = "\n".join(f"    case {n}: return {c};" for n, c in counts.items())
+    _write_if_changed(info, INFO.format(CASES=cases))
+    units.append(info)
     return units
 
 

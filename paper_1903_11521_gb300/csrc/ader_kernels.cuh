@@ -11,7 +11,12 @@
 //
 // Data layout in HBM ("element-blocked"): every per-element array is stored as
 // [tile][...entries...][32 lanes], so a warp's access to one entry of 32 elements is one
-// contiguous 256-byte segment.
+// contiguous segment.
+//
+// Precision: Real is the type of the bulk contractions (double, or float for the
+// precision form).  The DOFs Q, the time integral I and its accumulation over the
+// derivatives stay in double in both cases; the star matrices and flux solvers are set up
+// in double and stored as Real.
 //
 // Sparse products with the global matrices are straight-line code generated per degree
 // (codegen.py): every non-zero of the list is one fma with its value read at a fixed
@@ -33,10 +38,10 @@
 namespace yt {
 
 namespace gen {
-// Row<N, LIST, ROW>::dot(v, x) = sum over the non-zeros (l, value offset o) of row ROW of
-// sparse list LIST of v[o] * x[l * 9 * 32]; specialisations are generated per degree N
-// (codegen.py) with every non-zero unrolled.  Lists: 3*delta + x = derivative delta,
-// direction x; 18 + x = volume Khat^x; 21 + s = R^sT; 25 + s = Rhat^s.
+// Row<N, LIST, ROW>::dot<Real>(v, x) = sum over the non-zeros (l, value offset o) of row
+// ROW of sparse list LIST of v[o] * x[l * 9 * 32]; specialisations are generated per
+// degree N (codegen.py) with every non-zero unrolled.  Lists: 3*delta + x = derivative
+// delta, direction x; 18 + x = volume Khat^x; 21 + s = R^sT; 25 + s = Rhat^s.
 template <int N, int LIST, int ROW>
 struct Row;
 }  // namespace gen
@@ -72,33 +77,35 @@ struct Dims {
   }
 };
 
-// Offsets of the CSR lists in the table buffers (all row-pointer arrays share `rp`).
+// Global data of the step: the packed non-zero values of the sparse lists, the f^h
+// matrices (3 x BT x BT, column-major f[h][m + n*BT]) and the time-integral weights.
+// The derivatives are carried scaled, D~^d = dt^d D^d: the derivative lists hold
+// dt Ktilde^x, so D~^{d+1} = sum_x (dt Ktilde^x) D~^d Astar^xT, and the weights are
+// coeff[d] = dt / (d+1)!, which gives I = sum_d dt^{d+1}/(d+1)! D^d.  Magnitudes of D~
+// stay near those of Q (by the CFL condition), which keeps FP32 clear of overflow.
+template <typename Real>
 struct StepTables {
-  const int* rp;
-  const uint16_t* col;
-  const double* val;
-  const double* f;      // 3 x BT x BT dense, column-major (f[h][m + n*BT])
-  int ck[6][3];         // rp offset of the CK list for derivative delta, direction x
-  int vol[3];
-  int rT[4];
-  int rhat[4];
-  double coeff[8];      // dt^{d+1} / (d+1)!
+  const Real* val;
+  const Real* f;
+  double coeff[8];
 };
 
 // ------------------------------------------------------------------- CK derivatives
-// One derivative step delta -> delta+1, in place in Dsh (see the degree argument in the
-// solver's design notes: output row k only reads rows of higher polynomial degree, which
-// are overwritten later), accumulating the time integral in registers.
-template <int N, int DELTA>
-__device__ __forceinline__ void ck_step(const StepTables& T, const int (&scol)[3], int cnt,
-                                        double* __restrict__ Dsh, double* __restrict__ Xsh,
-                                        const double (&sc)[3][3], double (&Icol)[Dims<N>::B],
+// One derivative step delta -> delta+1, in place in Dsh: output row k only reads rows of
+// strictly higher polynomial degree (K~_kl != 0 only if deg phi_k < deg phi_l), so rows
+// processed in increasing order overwrite rows that are no longer needed.  The time
+// integral accumulates in double registers; only the C(N+2,3) rows that receive
+// derivative terms need one (rows of degree N hold c0 Q alone).
+template <int N, int DELTA, typename Real>
+__device__ __forceinline__ void ck_step(const StepTables<Real>& T, const int (&scol)[3], int cnt,
+                                        Real* __restrict__ Dsh, Real* __restrict__ Xsh,
+                                        const Real (&sc)[3][3], double (&Icol)[Dims<N>::nd(1)],
                                         int w, int lane) {
   using Dm = Dims<N>;
   if constexpr (DELTA < N) {
     constexpr int nout = Dm::nd(DELTA + 1);
     constexpr int KC = Dm::KC;
-    const double* xcol = Dsh + w * kTile + lane;
+    const Real* xcol = Dsh + w * kTile + lane;
     static_for<0, (nout + KC - 1) / KC>([&](auto chunk) {
       constexpr int k0 = decltype(chunk)::value * KC;
       // X^x[k][q] = sum_l Ktilde^x_kl D[l][q]  (this thread: column q = w)
@@ -115,43 +122,43 @@ __device__ __forceinline__ void ck_step(const StepTables& T, const int (&scol)[3
       static_for<0, KC>([&](auto kkc) {
         constexpr int kk = decltype(kkc)::value;
         if constexpr (k0 + kk < nout) {
-          double v = 0.0;
+          Real v = Real(0);
 #pragma unroll
           for (int x = 0; x < 3; ++x)
 #pragma unroll
             for (int s = 0; s < 3; ++s)
               if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
           Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
-          Icol[k0 + kk] = fma(T.coeff[DELTA + 1], v, Icol[k0 + kk]);
+          Icol[k0 + kk] = fma(T.coeff[DELTA + 1], (double)v, Icol[k0 + kk]);
         }
       });
       __syncthreads();
     });
-    ck_step<N, DELTA + 1>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+    ck_step<N, DELTA + 1, Real>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
   }
 }
 
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume and local flux of one tile of 32 elements.
-//   Q, Qout : [tile][9][B][32]   (may alias)
-//   Iout    : [tile][9][B][32]
-//   Pface   : [tile][4][9][BT][32]   projections R^sT I of the four faces
-//   star    : [tile][3][24][32]      non-zero slots of Astar^x
-//   floc    : [tile][4][9][9][32]    local flux solvers (row p, column q)
-//   Wloc    : [tile][4][9][BT][32]   (R^sT I) Aloc_s^T per face, written when LIFT is
-//                                    false (the full step lifts it together with the
-//                                    neighbour contribution in k_neigh)
+//   Q, Qout : [tile][9][B][32] double   (may alias)
+//   Iout    : [tile][9][B][32] double
+//   Pface   : [tile][4][9][BT][32]      projections R^sT I of the four faces
+//   star    : [tile][3][24][32]         non-zero slots of Astar^x
+//   floc    : [tile][4][9][9][32]       local flux solvers (row p, column q)
+//   Wloc    : [tile][4][9][BT][32]      (R^sT I) Aloc_s^T per face, written when LIFT is
+//                                       false (the full step lifts it together with the
+//                                       neighbour contribution in k_neigh)
 // LIFT = true applies the local flux here (Q is then the complete local update).
-template <int N, bool LIFT>
+template <int N, bool LIFT, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_local(const double* Q, double* Qout, double* __restrict__ Iout,
-        double* __restrict__ Pface, double* __restrict__ Wloc, const double* __restrict__ star,
-        const double* __restrict__ floc, StepTables T, StarPattern SP) {
+k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restrict__ Pface,
+        Real* __restrict__ Wloc, const Real* __restrict__ star, const Real* __restrict__ floc,
+        StepTables<Real> T, StarPattern SP) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
-  extern __shared__ double smem[];
-  double* Dsh = smem;                           // B rows x 9 x 32
-  double* Xsh = smem + B * kNq * kTile;         // XR rows x 9 x 32
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Dsh = reinterpret_cast<Real*>(smem_raw);  // B rows x 9 x 32
+  Real* Xsh = Dsh + B * kNq * kTile;               // XR rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const size_t tile = blockIdx.x;
@@ -162,39 +169,40 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
   int scol[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) scol[s] = (s < cnt) ? SP.col[s0 + s] : 0;
-  double sc[3][3];
+  Real sc[3][3];
 #pragma unroll
   for (int x = 0; x < 3; ++x)
 #pragma unroll
     for (int s = 0; s < 3; ++s)
-      sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : 0.0;
+      sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : Real(0);
 
-  double Icol[B];
+  constexpr int NI = Dm::nd(1);
+  double Icol[NI];
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const double q = __ldg(Qt + (w * B + k) * kTile + lane);
-    Dsh[(k * kNq + w) * kTile + lane] = q;
-    Icol[k] = T.coeff[0] * q;
+    Dsh[(k * kNq + w) * kTile + lane] = (Real)q;
+    if (k < NI) Icol[k < NI ? k : 0] = T.coeff[0] * q;
   }
   // (own column only is read before the first barrier)
-  ck_step<N, 0>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+  ck_step<N, 0, Real>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
 
   // publish I: shared (own column) and HBM
   double* It = Iout + tile * (kNq * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    Dsh[(k * kNq + w) * kTile + lane] = Icol[k];
-    It[(w * B + k) * kTile + lane] = Icol[k];
+    const double ik = k < NI ? Icol[k < NI ? k : 0] : T.coeff[0] * Qt[(w * B + k) * kTile + lane];
+    Dsh[(k * kNq + w) * kTile + lane] = (Real)ik;
+    It[(w * B + k) * kTile + lane] = ik;
   }
 
-  // With LIFT the local flux is added to every row after the volume term, so the update
-  // is accumulated in registers; without it the volume term completes each row of Q,
-  // which is written as soon as its chunk is done.
-  double dQ[LIFT ? B : 1];
+  // The volume term is added to each row of Q as soon as its chunk is done; with LIFT the
+  // local flux is then added face by face (every row of an element column belongs to
+  // one thread, so these read-modify-writes need no synchronisation).
   double* Qo = Qout + tile * (kNq * B * kTile);
 
   // volume: dQ[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q]
-  const double* icol = Dsh + w * kTile + lane;
+  const Real* icol = Dsh + w * kTile + lane;
   static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
     constexpr int k0 = decltype(chunk)::value * KC;
     static_for<0, KC>([&](auto kkc) {
@@ -210,38 +218,37 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
       constexpr int kk = decltype(kkc)::value;
       if constexpr (k0 + kk < B) {
         constexpr int k = k0 + kk;
-        double v = 0.0;
+        Real v = Real(0);
 #pragma unroll
         for (int x = 0; x < 3; ++x)
 #pragma unroll
           for (int s = 0; s < 3; ++s)
             if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-        if constexpr (LIFT) dQ[k] = v;
-        else Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + v;
+        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + (double)v;
       }
     });
     __syncthreads();
   });
 
   // local flux: dQ += Rhat^s ((R^sT I) Aloc_s^T)
-  double* Pt = Pface + tile * (4 * kNq * BT * kTile);
-  const double* Ft = floc + tile * (4 * kNq * kNq * kTile);
+  Real* Pt = Pface + tile * (4 * kNq * BT * kTile);
+  const Real* Ft = floc + tile * (4 * kNq * kNq * kTile);
   static_for<0, 4>([&](auto face) {
     constexpr int s = decltype(face)::value;
     static_for<0, BT>([&](auto mm) {
       constexpr int m = decltype(mm)::value;
-      const double z = gen::Row<N, 21 + s, m>::dot(T.val, icol);
+      const Real z = gen::Row<N, 21 + s, m>::dot(T.val, icol);
       Xsh[(m * kNq + w) * kTile + lane] = z;
       Pt[((s * kNq + w) * BT + m) * kTile + lane] = z;
     });
-    double a[kNq];
+    Real a[kNq];
 #pragma unroll
     for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
     __syncthreads();
-    double Wr[BT];
+    Real Wr[BT];
 #pragma unroll
     for (int m = 0; m < BT; ++m) {
-      double v = 0.0;
+      Real v = Real(0);
 #pragma unroll
       for (int q = 0; q < kNq; ++q) v = fma(a[q], Xsh[(m * kNq + q) * kTile + lane], v);
       Wr[m] = v;
@@ -250,22 +257,18 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
     if constexpr (LIFT) {
 #pragma unroll
       for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
-      const double* wcol = Xsh + w * kTile + lane;
+      const Real* wcol = Xsh + w * kTile + lane;
       static_for<0, B>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        dQ[k] += gen::Row<N, 25 + s, k>::dot(T.val, wcol);
+        Qo[(w * B + k) * kTile + lane] += (double)gen::Row<N, 25 + s, k>::dot(T.val, wcol);
       });
     } else {
-      double* Wt = Wloc + tile * (4 * kNq * BT * kTile);
+      Real* Wt = Wloc + tile * (4 * kNq * BT * kTile);
 #pragma unroll
       for (int m = 0; m < BT; ++m) Wt[((s * kNq + w) * BT + m) * kTile + lane] = Wr[m];
     }
   });
 
-  if constexpr (LIFT) {
-#pragma unroll
-    for (int k = 0; k < B; ++k) Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + dQ[k];
-  }
 }
 
 // ------------------------------------------------------------------------- K_neigh
@@ -274,54 +277,53 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout,
 //   conn : [E_pad][4] packed (neighbour << 4) | (j << 2) | h
 // WITH_LOCAL: add the local flux terms Wloc written by k_local<N, false> before lifting,
 // so that Rhat^s is applied once per face to the sum of both flux contributions.
-template <int N, bool WITH_LOCAL>
+// The four faces' W (BT x 9 each) stay in shared memory; every row k of Q is then
+// updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
+template <int N, bool WITH_LOCAL, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ Wloc,
-        const double* __restrict__ fnb, const int* __restrict__ conn, StepTables T) {
+k_neigh(double* Q, const Real* __restrict__ Pface, const Real* __restrict__ Wloc,
+        const Real* __restrict__ fnb, const int* __restrict__ conn, StepTables<Real> T) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT;
-  extern __shared__ double smem[];
-  double* Xsh = smem;                           // BT rows x 9 x 32
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Wsh = reinterpret_cast<Real*>(smem_raw);  // 4 faces x BT rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const size_t tile = blockIdx.x;
   const size_t e = tile * kTile + lane;
-
-  double dQ[B];
-#pragma unroll
-  for (int k = 0; k < B; ++k) dQ[k] = 0.0;
-  const double* Ft = fnb + tile * (4 * kNq * kNq * kTile);
+  const Real* Ft = fnb + tile * (4 * kNq * kNq * kTile);
 
   static_for<0, 4>([&](auto face) {
     constexpr int s = decltype(face)::value;
+    Real* Xsh = Wsh + s * BT * kNq * kTile;
     const int c = __ldg(conn + e * 4 + s);
     const size_t nb = (size_t)(c >> 4);
     const int j = (c >> 2) & 3, h = c & 3;
-    const double* P = Pface + ((((nb / kTile) * 4 + j) * kNq + w) * BT) * kTile + (nb % kTile);
-    double Pn[BT];
+    const Real* P = Pface + ((((nb / kTile) * 4 + j) * kNq + w) * BT) * kTile + (nb % kTile);
+    Real Pn[BT];
 #pragma unroll
     for (int n = 0; n < BT; ++n) Pn[n] = __ldg(P + n * kTile);
-    const double* fh = T.f + (size_t)h * BT * BT;
+    const Real* fh = T.f + (size_t)h * BT * BT;
     // V[m][q] = sum_n f^h_mn Pn[n], f^h block-diagonal by polynomial degree
 #pragma unroll
     for (int d = 0; d <= N; ++d) {
       const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
 #pragma unroll
       for (int m = lo; m < hi; ++m) {
-        double v = 0.0;
+        Real v = Real(0);
 #pragma unroll
         for (int n = lo; n < hi; ++n) v = fma(__ldg(fh + m + n * BT), Pn[n], v);
         Xsh[(m * kNq + w) * kTile + lane] = v;
       }
     }
-    double a[kNq];
+    Real a[kNq];
 #pragma unroll
     for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
     __syncthreads();
-    double Wr[BT];
+    Real Wr[BT];
 #pragma unroll
     for (int m = 0; m < BT; ++m) {
-      double v = 0.0;
+      Real v = Real(0);
       if constexpr (WITH_LOCAL) v = __ldg(Wloc + ((tile * 4 + s) * kNq * BT + w * BT + m) * kTile + lane);
 #pragma unroll
       for (int q = 0; q < kNq; ++q) v = fma(a[q], Xsh[(m * kNq + q) * kTile + lane], v);
@@ -330,80 +332,94 @@ k_neigh(double* Q, const double* __restrict__ Pface, const double* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
-    const double* wcol = Xsh + w * kTile + lane;
-    static_for<0, B>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      dQ[k] += gen::Row<N, 25 + s, k>::dot(T.val, wcol);
-    });
   });
+  // every thread reads only its own columns of Wsh below: no barrier needed
   double* Qt = Q + tile * (kNq * B * kTile);
-#pragma unroll
-  for (int k = 0; k < B; ++k) Qt[(w * B + k) * kTile + lane] += dQ[k];
+  static_for<0, B>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const Real* wcol = Wsh + w * kTile + lane;
+    double dq = (double)gen::Row<N, 25, k>::dot(T.val, wcol);
+    dq += (double)gen::Row<N, 26, k>::dot(T.val, wcol + 1 * BT * kNq * kTile);
+    dq += (double)gen::Row<N, 27, k>::dot(T.val, wcol + 2 * BT * kNq * kTile);
+    dq += (double)gen::Row<N, 28, k>::dot(T.val, wcol + 3 * BT * kNq * kTile);
+    Qt[(w * B + k) * kTile + lane] += dq;
+  });
 }
 
 // ------------------------------------------------------------------ launch helpers
+// Buffers typed by the contraction type are passed untyped and cast by the per-degree,
+// per-precision launch functions.
 struct AderLaunch {
   int64_t ntiles;
   size_t smem_local, smem_neigh;
-  double *Q, *I, *Pface, *Wloc;
-  const double *star, *floc, *fnb;
+  double *Q, *I;
+  void *Pface, *Wloc;
+  const void *star, *floc, *fnb, *val, *f;
   const int* conn;
-  StepTables T;
+  double coeff[8];
   StarPattern SP;
   cudaStream_t stream;
 };
 
-template <int N>
-void ader_set_attributes(size_t smem_local, size_t smem_neigh) {
-  cudaFuncSetAttribute(k_local<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_local);
-  cudaFuncSetAttribute(k_local<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_local);
-  cudaFuncSetAttribute(k_neigh<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_neigh);
-  cudaFuncSetAttribute(k_neigh<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_neigh);
+template <typename Real>
+StepTables<Real> step_tables(const AderLaunch& L) {
+  StepTables<Real> T;
+  T.val = static_cast<const Real*>(L.val);
+  T.f = static_cast<const Real*>(L.f);
+  for (int i = 0; i < 8; ++i) T.coeff[i] = L.coeff[i];
+  return T;
 }
 
-// fused = true: the local half of the full step (local flux lifted in k_neigh)
-template <int N>
-void ader_launch_local(const AderLaunch& L, bool fused) {
-  const unsigned grid = (unsigned)L.ntiles;
-  if (fused)
-    k_local<N, false><<<grid, kNq * kTile, L.smem_local, L.stream>>>(L.Q, L.Q, L.I, L.Pface, L.Wloc,
-                                                                       L.star, L.floc, L.T, L.SP);
+// Launch functions of one kernel variant (LOCAL: k_local<N, !FUSED>; else
+// k_neigh<N, FUSED>); the generated translation units instantiate one variant each.
+template <int N, typename Real, bool LOCAL, bool FUSED>
+void ader_set_attribute(size_t smem) {
+  if constexpr (LOCAL)
+    cudaFuncSetAttribute(k_local<N, !FUSED, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else
-    k_local<N, true><<<grid, kNq * kTile, L.smem_local, L.stream>>>(L.Q, L.Q, L.I, L.Pface, L.Wloc,
-                                                                      L.star, L.floc, L.T, L.SP);
+    cudaFuncSetAttribute(k_neigh<N, FUSED, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int N>
-void ader_launch_neigh(const AderLaunch& L, bool fused) {
+template <int N, typename Real, bool LOCAL, bool FUSED>
+void ader_launch(const AderLaunch& L) {
   const unsigned grid = (unsigned)L.ntiles;
-  if (fused)
-    k_neigh<N, true><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(L.Q, L.Pface, L.Wloc, L.fnb,
-                                                                      L.conn, L.T);
-  else
-    k_neigh<N, false><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(L.Q, L.Pface, L.Wloc, L.fnb,
-                                                                       L.conn, L.T);
+  const StepTables<Real> T = step_tables<Real>(L);
+  if constexpr (LOCAL) {
+    k_local<N, !FUSED, Real><<<grid, kNq * kTile, L.smem_local, L.stream>>>(
+        L.Q, L.Q, L.I, static_cast<Real*>(L.Pface), static_cast<Real*>(L.Wloc),
+        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP);
+  } else {
+    k_neigh<N, FUSED, Real><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(
+        L.Q, static_cast<const Real*>(L.Pface), static_cast<const Real*>(L.Wloc),
+        static_cast<const Real*>(L.fnb), L.conn, T);
+  }
 }
 
-// per-degree instantiations live in generated translation units
-void ader_set_attributes_o1(size_t, size_t);
-void ader_set_attributes_o2(size_t, size_t);
-void ader_set_attributes_o3(size_t, size_t);
-void ader_set_attributes_o4(size_t, size_t);
-void ader_set_attributes_o5(size_t, size_t);
-void ader_launch_local_o1(const AderLaunch&, bool);
-void ader_launch_local_o2(const AderLaunch&, bool);
-void ader_launch_local_o3(const AderLaunch&, bool);
-void ader_launch_local_o4(const AderLaunch&, bool);
-void ader_launch_local_o5(const AderLaunch&, bool);
-void ader_launch_neigh_o1(const AderLaunch&, bool);
-void ader_launch_neigh_o2(const AderLaunch&, bool);
-void ader_launch_neigh_o3(const AderLaunch&, bool);
-void ader_launch_neigh_o4(const AderLaunch&, bool);
-void ader_launch_neigh_o5(const AderLaunch&, bool);
-int ader_generated_nnz_o1();
-int ader_generated_nnz_o2();
-int ader_generated_nnz_o3();
-int ader_generated_nnz_o4();
-int ader_generated_nnz_o5();
+// Per-degree, per-precision, per-variant instantiations live in generated translation
+// units (ader_o<N>_<f64|f32>_<variant>.cu, variant = lf: local fused, ll: local lifted,
+// nf: neighbour fused, np: neighbour plain).  Degree 6 exists in f32 only: its FP64
+// shared-memory footprint (258 KB) exceeds the 227 KB a CTA may use.
+#define YT_DECLARE_ADER_VARIANT(N, P, V)                  \
+  void ader_set_attribute_o##N##_##P##_##V(size_t);      \
+  void ader_launch_o##N##_##P##_##V(const AderLaunch&);
+#define YT_DECLARE_ADER_UNIT(N, P)     \
+  YT_DECLARE_ADER_VARIANT(N, P, lf)    \
+  YT_DECLARE_ADER_VARIANT(N, P, ll)    \
+  YT_DECLARE_ADER_VARIANT(N, P, nf)    \
+  YT_DECLARE_ADER_VARIANT(N, P, np)
+YT_DECLARE_ADER_UNIT(1, f64)
+YT_DECLARE_ADER_UNIT(2, f64)
+YT_DECLARE_ADER_UNIT(3, f64)
+YT_DECLARE_ADER_UNIT(4, f64)
+YT_DECLARE_ADER_UNIT(5, f64)
+YT_DECLARE_ADER_UNIT(1, f32)
+YT_DECLARE_ADER_UNIT(2, f32)
+YT_DECLARE_ADER_UNIT(3, f32)
+YT_DECLARE_ADER_UNIT(4, f32)
+YT_DECLARE_ADER_UNIT(5, f32)
+YT_DECLARE_ADER_UNIT(6, f32)
+#undef YT_DECLARE_ADER_UNIT
+#undef YT_DECLARE_ADER_VARIANT
+int ader_generated_nnz(int N);
 
 }  // namespace yt

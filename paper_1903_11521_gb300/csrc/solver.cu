@@ -145,6 +145,11 @@ __global__ void k_from_blocked(const double* __restrict__ in, double* __restrict
   out[i] = in[(((e / kTile) * kNq + q) * B + k) * kTile + (e % kTile)];
 }
 
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
 // --------------------------------------------------------------------- host helpers
 struct Csr {
   std::vector<int> rp;
@@ -152,8 +157,9 @@ struct Csr {
   std::vector<double> val;
   // Appends the CSR of a rows x cols view; `at(r, c)` gives the entry.  Returns the rp
   // offset.  Flops of the lists are accumulated by the caller.
+  // Values are stored multiplied by `scale`; the pattern is that of the unscaled entries.
   template <typename F>
-  int add(int rows, int cols, F at) {
+  int add(int rows, int cols, F at, double scale = 1.0) {
     const int off = static_cast<int>(rp.size());
     for (int r = 0; r < rows; ++r) {
       rp.push_back(static_cast<int>(col.size()));
@@ -161,7 +167,7 @@ struct Csr {
         const double v = at(r, c);
         if (v != 0.0) {
           col.push_back(static_cast<uint16_t>(c));
-          val.push_back(v);
+          val.push_back(v * scale);
         }
       }
     }
@@ -186,22 +192,26 @@ struct yt_solver {
   yt_precision prec = YT_F64;
   double dt = 0.0;
   bool has_neighbours = false;
-  double *Q = nullptr, *I = nullptr, *Pface = nullptr, *Wloc = nullptr, *star = nullptr,
-         *floc = nullptr, *fnb = nullptr, *staging = nullptr;
+  double *Q = nullptr, *I = nullptr, *star = nullptr, *floc = nullptr, *fnb = nullptr,
+         *staging = nullptr;
+  // buffers of the contraction type (double for YT_F64, float for YT_F32)
+  void *Pface = nullptr, *Wloc = nullptr, *star_r = nullptr, *floc_r = nullptr, *fnb_r = nullptr;
   int* conn = nullptr;
-  int* d_rp = nullptr;
-  uint16_t* d_col = nullptr;
   double* d_val = nullptr;
   double* d_f = nullptr;
-  StepTables T{};
+  float* d_val32 = nullptr;
+  float* d_f32 = nullptr;
+  double coeff[8] = {0};
+  size_t real_bytes = 8;
   double flops_local = 0, flops_neigh = 0, bytes_local = 0, bytes_neigh = 0;
   double flops_local_unfused = 0;
   int64_t n_values = 0;
   size_t smem_local = 0, smem_neigh = 0;
   ~yt_solver() {
-    for (void* p : {(void*)Q, (void*)I, (void*)Pface, (void*)Wloc, (void*)star, (void*)floc, (void*)fnb,
-                    (void*)staging, (void*)conn, (void*)d_rp, (void*)d_col, (void*)d_val,
-                    (void*)d_f})
+    if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
+    for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
+                    floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
+                    (void*)d_val32, (void*)d_f32})
       if (p) cudaFree(p);
   }
 };
@@ -217,73 +227,70 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.I = s->I;
   L.Pface = s->Pface;
   L.Wloc = s->Wloc;
-  L.star = s->star;
-  L.floc = s->floc;
-  L.fnb = s->fnb;
+  L.star = s->star_r;
+  L.floc = s->floc_r;
+  L.fnb = s->fnb_r;
   L.conn = s->conn;
-  L.T = s->T;
+  const bool f32 = s->prec == YT_F32;
+  L.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
+  L.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
+  for (int i = 0; i < 8; ++i) L.coeff[i] = s->coeff[i];
   L.SP = kStar;
   L.stream = st;
   return L;
 }
 
-// Shared memory of the two kernels of degree N (FP64): k_local holds the B-row column
-// buffer and the exchange buffer, k_neigh the exchange buffer only.
+#define YT_VARIANT_SWITCH(FN, V, ...)                                          \
+  do {                                                                         \
+    switch (s->N * 2 + (s->prec == YT_F32 ? 1 : 0)) {                          \
+      case 2: FN##_o1_f64_##V(__VA_ARGS__); break;                            \
+      case 3: FN##_o1_f32_##V(__VA_ARGS__); break;                            \
+      case 4: FN##_o2_f64_##V(__VA_ARGS__); break;                            \
+      case 5: FN##_o2_f32_##V(__VA_ARGS__); break;                            \
+      case 6: FN##_o3_f64_##V(__VA_ARGS__); break;                            \
+      case 7: FN##_o3_f32_##V(__VA_ARGS__); break;                            \
+      case 8: FN##_o4_f64_##V(__VA_ARGS__); break;                            \
+      case 9: FN##_o4_f32_##V(__VA_ARGS__); break;                            \
+      case 10: FN##_o5_f64_##V(__VA_ARGS__); break;                           \
+      case 11: FN##_o5_f32_##V(__VA_ARGS__); break;                           \
+      case 13: FN##_o6_f32_##V(__VA_ARGS__); break;                           \
+      default: throw Error(YT_ERR_UNSUPPORTED, "no kernel for this order and precision"); \
+    }                                                                          \
+  } while (0)
+
+// Shared memory of the two kernels of degree N: k_local holds the B-row column buffer
+// and the exchange buffer, k_neigh the four faces' flux products.
 void set_smem(yt_solver* s) {
   const int N = s->N;
   const int B = n_basis(N), BT = n_face_basis(N);
   const int KC = BT / 3 > 0 ? BT / 3 : 1;
   const int XR = 3 * KC > BT ? 3 * KC : BT;
-  s->smem_local = sizeof(double) * (size_t)(B + XR) * kNq * kTile;
-  s->smem_neigh = sizeof(double) * (size_t)BT * kNq * kTile;
-  switch (N) {
-    case 1: ader_set_attributes_o1(s->smem_local, s->smem_neigh); break;
-    case 2: ader_set_attributes_o2(s->smem_local, s->smem_neigh); break;
-    case 3: ader_set_attributes_o3(s->smem_local, s->smem_neigh); break;
-    case 4: ader_set_attributes_o4(s->smem_local, s->smem_neigh); break;
-    case 5: ader_set_attributes_o5(s->smem_local, s->smem_neigh); break;
-    default: throw Error(YT_ERR_UNSUPPORTED, "FP64 solver supports orders 2..6");
-  }
+  s->smem_local = s->real_bytes * (size_t)(B + XR) * kNq * kTile;
+  s->smem_neigh = s->real_bytes * (size_t)(4 * BT) * kNq * kTile;
+  YT_REQUIRE(s->smem_local <= 227 * 1024 && s->smem_neigh <= 227 * 1024, YT_ERR_UNSUPPORTED,
+             "order too high for this precision");
+  YT_VARIANT_SWITCH(ader_set_attribute, lf, s->smem_local);
+  YT_VARIANT_SWITCH(ader_set_attribute, ll, s->smem_local);
+  YT_VARIANT_SWITCH(ader_set_attribute, nf, s->smem_neigh);
+  YT_VARIANT_SWITCH(ader_set_attribute, np, s->smem_neigh);
   cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
-}
-
-int generated_nnz(int N) {
-  switch (N) {
-    case 1: return ader_generated_nnz_o1();
-    case 2: return ader_generated_nnz_o2();
-    case 3: return ader_generated_nnz_o3();
-    case 4: return ader_generated_nnz_o4();
-    case 5: return ader_generated_nnz_o5();
-  }
-  return -1;
 }
 
 void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
   const AderLaunch L = launch_args(s, st);
-  switch (s->N) {
-    case 1: ader_launch_local_o1(L, fused); break;
-    case 2: ader_launch_local_o2(L, fused); break;
-    case 3: ader_launch_local_o3(L, fused); break;
-    case 4: ader_launch_local_o4(L, fused); break;
-    case 5: ader_launch_local_o5(L, fused); break;
-    default: throw Error(YT_ERR_UNSUPPORTED, "order");
-  }
+  if (fused) YT_VARIANT_SWITCH(ader_launch, lf, L);
+  else YT_VARIANT_SWITCH(ader_launch, ll, L);
   cuda_check(cudaGetLastError(), "k_local launch");
 }
 void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
   const AderLaunch L = launch_args(s, st);
-  switch (s->N) {
-    case 1: ader_launch_neigh_o1(L, fused); break;
-    case 2: ader_launch_neigh_o2(L, fused); break;
-    case 3: ader_launch_neigh_o3(L, fused); break;
-    case 4: ader_launch_neigh_o4(L, fused); break;
-    case 5: ader_launch_neigh_o5(L, fused); break;
-    default: throw Error(YT_ERR_UNSUPPORTED, "order");
-  }
+  if (fused) YT_VARIANT_SWITCH(ader_launch, nf, L);
+  else YT_VARIANT_SWITCH(ader_launch, np, L);
   cuda_check(cudaGetLastError(), "k_neigh launch");
 }
 
-// Builds the CSR tables of one order and the flop / byte counts of the two kernels.
+// Packs the non-zero values of the sparse lists of one order (in the order the generated
+// kernels read them) and counts the flops / bytes of the two kernels.
 void build_tables(yt_solver* s) {
   const RefMatrices& R = reference_matrices(s->N);
   const int N = s->N, B = R.B, BT = R.BT;
@@ -294,26 +301,28 @@ void build_tables(yt_solver* s) {
     const int nin = nd(delta), nout = nd(delta + 1);
     for (int x = 0; x < 3; ++x) {
       const double* K = R.Ktilde.data() + (size_t)x * B * B;
-      s->T.ck[delta][x] = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; });
-      for (int r = 0; r < nout; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.ck[delta][x], r) + 1.0);
+      // derivatives are carried scaled by dt^delta (D~ = dt^delta D), so the values of the
+      // derivative lists are dt Ktilde: magnitudes stay near those of Q, also in FP32
+      const int off = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; }, s->dt);
+      for (int r = 0; r < nout; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off, r) + 1.0);
     }
     fl += nout * (2.0 * 3 * kStarSlots + 2.0 * 9);        // mixing + time integral
   }
   for (int x = 0; x < 3; ++x) {
     const double* K = R.Khat.data() + (size_t)x * B * B;
-    s->T.vol[x] = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
-    for (int r = 0; r < B; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.vol[x], r) + 1.0);
+    const int off = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
+    for (int r = 0; r < B; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off, r) + 1.0);
   }
   fl += B * 2.0 * 3 * kStarSlots;
   double fn = 0.0, lift_total = 0.0;
   for (int f = 0; f < 4; ++f) {
     const double* Rs = R.R.data() + (size_t)f * B * BT;
     const double* Rh = R.Rhat.data() + (size_t)f * B * BT;
-    s->T.rT[f] = csr.add(BT, B, [&](int r, int c) { return Rs[c + (size_t)r * B]; });
-    s->T.rhat[f] = csr.add(B, BT, [&](int r, int c) { return Rh[r + (size_t)c * B]; });
+    const int off_rt = csr.add(BT, B, [&](int r, int c) { return Rs[c + (size_t)r * B]; });
+    const int off_rh = csr.add(B, BT, [&](int r, int c) { return Rh[r + (size_t)c * B]; });
     double lift = 0.0;
-    for (int r = 0; r < BT; ++r) fl += 9.0 * (2.0 * csr.row_nnz(s->T.rT[f], r) + 1.0);
-    for (int r = 0; r < B; ++r) lift += 9.0 * (2.0 * csr.row_nnz(s->T.rhat[f], r) + 1.0 + 1.0);
+    for (int r = 0; r < BT; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off_rt, r) + 1.0);
+    for (int r = 0; r < B; ++r) lift += 9.0 * (2.0 * csr.row_nnz(off_rh, r) + 1.0 + 1.0);
     fl += BT * 2.0 * 81;
     lift_total += lift;
     double blocks = 0.0;
@@ -327,27 +336,27 @@ void build_tables(yt_solver* s) {
   s->flops_local = fl;
   s->flops_neigh = fn + 4.0 * 9 * BT;
   s->flops_local_unfused = fl + lift_total;
-  const double qb = 8.0 * 9 * B, pb = 8.0 * 4 * 9 * BT;
-  s->bytes_local = 3 * qb + 2 * pb + 8.0 * (3 * kStarSlots + 4 * 81);   // + Wloc written
-  s->bytes_neigh = 2 * qb + 2 * pb + 8.0 * 4 * 81 + 16.0;               // + Wloc read
+  const double rb = (double)s->real_bytes;
+  const double qb = 8.0 * 9 * B, pb = rb * 4 * 9 * BT;
+  s->bytes_local = 3 * qb + 2 * pb + rb * (3 * kStarSlots + 4 * 81);   // + Wloc written
+  s->bytes_neigh = 2 * qb + 2 * pb + rb * 4 * 81 + 16.0;               // + Wloc read
   if (csr.col.size() > 0x7fffffff) throw Error(YT_ERR_UNSUPPORTED, "tables too large");
   s->n_values = (int64_t)csr.val.size();
-  s->d_rp = dalloc<int>(csr.rp.size());
-  s->d_col = dalloc<uint16_t>(csr.col.size());
   s->d_val = dalloc<double>(csr.val.size());
   s->d_f = dalloc<double>(R.f.size());
-  cuda_check(cudaMemcpy(s->d_rp, csr.rp.data(), csr.rp.size() * sizeof(int), cudaMemcpyHostToDevice), "copy rp");
-  cuda_check(cudaMemcpy(s->d_col, csr.col.data(), csr.col.size() * sizeof(uint16_t), cudaMemcpyHostToDevice), "copy col");
   cuda_check(cudaMemcpy(s->d_val, csr.val.data(), csr.val.size() * sizeof(double), cudaMemcpyHostToDevice), "copy val");
   cuda_check(cudaMemcpy(s->d_f, R.f.data(), R.f.size() * sizeof(double), cudaMemcpyHostToDevice), "copy f");
-  s->T.rp = s->d_rp;
-  s->T.col = s->d_col;
-  s->T.val = s->d_val;
-  s->T.f = s->d_f;
-  double c = 1.0;
+  if (s->prec == YT_F32) {
+    std::vector<float> v32(csr.val.begin(), csr.val.end()), f32(R.f.begin(), R.f.end());
+    s->d_val32 = dalloc<float>(v32.size());
+    s->d_f32 = dalloc<float>(f32.size());
+    cuda_check(cudaMemcpy(s->d_val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy val32");
+    cuda_check(cudaMemcpy(s->d_f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy f32");
+  }
+  double c = s->dt;
   for (int d = 0; d <= N && d < 8; ++d) {
-    c *= s->dt / (d + 1.0);
-    s->T.coeff[d] = c;                                     // dt^{d+1}/(d+1)!
+    c /= (d + 1.0);
+    s->coeff[d] = c;        // dt^{d+1}/(d+1)! D^d = dt/(d+1)! D~^d with D~^d = dt^d D^d
   }
 }
 
@@ -364,8 +373,10 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
                "mesh needs n_elements > 0, material and jacobian");
     YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
     YT_REQUIRE(scheme->order >= 2 && scheme->order <= 7, YT_ERR_INVALID, "order must be 2..7");
-    YT_REQUIRE(scheme->precision == YT_F64, YT_ERR_UNSUPPORTED, "solver precision: YT_F64 only in this build");
-    YT_REQUIRE(scheme->order <= 6, YT_ERR_UNSUPPORTED, "FP64 solver: orders 2..6 in this build");
+    YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32, YT_ERR_UNSUPPORTED,
+               "solver precision: YT_F64 or YT_F32");
+    YT_REQUIRE(scheme->precision == YT_F32 || scheme->order <= 6, YT_ERR_UNSUPPORTED,
+               "YT_F64 solver: orders 2..6 (order 7 needs YT_F32)");
     YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
     YT_REQUIRE(mesh->n_elements < (int64_t(1) << 27), YT_ERR_UNSUPPORTED, "at most 2^27 elements");
     const bool nb = mesh->neighbours != nullptr;
@@ -378,6 +389,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     s->ntiles = (s->E + kTile - 1) / kTile;
     s->Epad = s->ntiles * kTile;
     s->prec = scheme->precision;
+    s->real_bytes = s->prec == YT_F32 ? sizeof(float) : sizeof(double);
     s->dt = scheme->dt;
     s->has_neighbours = nb;
     std::vector<int> conn;
@@ -393,22 +405,22 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
         }
     }
     build_tables(s.get());
-    YT_REQUIRE(generated_nnz(s->N) == (int)s->n_values, YT_ERR_INVALID,
+    YT_REQUIRE(ader_generated_nnz(s->N) == (int)s->n_values, YT_ERR_INVALID,
                "generated kernels do not match the reference matrices (rebuild the library)");
     set_smem(s.get());
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t nq = (size_t)s->Epad * kNq * s->B;
     s->Q = dalloc<double>(nq);
     s->I = dalloc<double>(nq);
-    s->Pface = dalloc<double>((size_t)s->Epad * 4 * kNq * s->BT);
-    s->Wloc = dalloc<double>((size_t)s->Epad * 4 * kNq * s->BT);
+    s->Pface = dalloc<unsigned char>((size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes);
+    s->Wloc = dalloc<unsigned char>((size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes);
     s->star = dalloc<double>((size_t)s->Epad * 3 * kStarSlots);
     s->floc = dalloc<double>((size_t)s->Epad * 4 * 81);
     s->fnb = dalloc<double>((size_t)s->Epad * 4 * 81);
     s->conn = dalloc<int>((size_t)s->Epad * 4);
     cuda_check(cudaMemsetAsync(s->Q, 0, nq * sizeof(double), st), "memset Q");
     cuda_check(cudaMemsetAsync(s->I, 0, nq * sizeof(double), st), "memset I");
-    cuda_check(cudaMemsetAsync(s->Pface, 0, (size_t)s->Epad * 4 * kNq * s->BT * sizeof(double), st), "memset P");
+    cuda_check(cudaMemsetAsync(s->Pface, 0, (size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes, st), "memset P");
     cuda_check(cudaMemsetAsync(s->conn, 0, (size_t)s->Epad * 4 * sizeof(int), st), "memset conn");
     if (nb) cuda_check(cudaMemcpyAsync(s->conn, conn.data(), conn.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy conn");
     double* dmat = dalloc<double>((size_t)s->E * 3);
@@ -420,6 +432,22 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) {
       k_setup<<<blocks_for(s->Epad, 128), 128, 0, st>>>(dmat, djac, s->E, s->Epad, s->star, s->floc, s->fnb);
       e1 = cudaGetLastError();
+    }
+    if (e1 == cudaSuccess) {
+      if (s->prec == YT_F32) {
+        const int64_t ns = s->Epad * 3 * kStarSlots, nf = s->Epad * 4 * 81;
+        s->star_r = dalloc<float>((size_t)ns);
+        s->floc_r = dalloc<float>((size_t)nf);
+        s->fnb_r = dalloc<float>((size_t)nf);
+        k_to_float<<<blocks_for(ns, 256), 256, 0, st>>>(s->star, static_cast<float*>(s->star_r), ns);
+        k_to_float<<<blocks_for(nf, 256), 256, 0, st>>>(s->floc, static_cast<float*>(s->floc_r), nf);
+        k_to_float<<<blocks_for(nf, 256), 256, 0, st>>>(s->fnb, static_cast<float*>(s->fnb_r), nf);
+        e1 = cudaGetLastError();
+      } else {
+        s->star_r = s->star;
+        s->floc_r = s->floc;
+        s->fnb_r = s->fnb;
+      }
     }
     cudaError_t e5 = cudaStreamSynchronize(st);
     cudaFree(dmat);

@@ -146,3 +146,62 @@ def test_phases_equal_step_and_unfused_path(yt):
         s.close()
     assert np.array_equal(outs[0], outs[1])
     assert rel_per_quantity(outs[2], outs[0]).max() < TOL
+
+
+# ------------------------------------------------------------------ precision form (FP32)
+F32_TOL_INCREMENT = 2e-5     # relative Frobenius norm per quantity of Q_new - Q
+F32_TOL_I = 2e-6             # of the time integral
+
+
+def run_gpu_prec(yt, el, conn, Q, dt, order, precision, full=True, steps=1):
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    s = yt.Solver(order, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient, precision=precision)
+    s.set_dofs_host(Q)
+    for _ in range(steps):
+        s.step() if full else s.step_local()
+    q = s.get_host(yt.YT_FIELD_DOFS)
+    i = s.get_host(yt.YT_FIELD_TIME_INTEGRAL)
+    s.close()
+    return q, i
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+def test_f32_full_step_against_fp64_oracle(yt, order):
+    """Bulk contractions in FP32, setup / time-integral accumulation / DOFs in FP64."""
+    el, conn, Q, dt = make_case(70, order, "impedance", seed=31)
+    q32, i32 = run_gpu_prec(yt, el, conn, Q, dt, order, yt.YT_F32)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    q_ref, I = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
+                                dt, order - 1)
+    assert rel_per_quantity(i32, I).max() < F32_TOL_I
+    assert rel_per_quantity(q32 - Q, q_ref - Q).max() < F32_TOL_INCREMENT
+
+
+def test_f32_local_step_order7(yt):
+    el, conn, Q, dt = make_case(45, 7, "impedance", seed=32)
+    q32, i32 = run_gpu_prec(yt, el, conn, Q, dt, 7, yt.YT_F32, full=False)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    _, I = scheme.derivatives_and_time_integral(Q, star, dt, 6)
+    q_ref = scheme.local_update(Q, I, star, loc, 6)
+    assert rel_per_quantity(i32, I).max() < F32_TOL_I
+    assert rel_per_quantity(q32 - Q, q_ref - Q).max() < F32_TOL_INCREMENT
+
+
+def test_f32_plane_wave_100_steps(yt):
+    """100 steps at order 5 on the periodic mesh: the FP32 form stays within a stated
+    bound of the FP64 path (itself equal to the oracle step by step) and its plane-wave
+    error equals the FP64 one to 1e-3 relative."""
+    order, N = 5, 4
+    k = 2 * np.pi * np.array([1.0, 1.0, 0.0])
+    mesh = wl.periodic_cube_mesh(3)
+    el = mesh.elements
+    dt = wl.cfl_time_step(el, N, cfl=0.3)
+    T = 100 * dt
+    Q0 = planewave.project(mesh, N, 0.0, k, 1.0, 2.0, 1.0)
+    q64, _ = run_gpu_prec(yt, el, mesh.conn, Q0, dt, order, yt.YT_F64, steps=100)
+    q32, _ = run_gpu_prec(yt, el, mesh.conn, Q0, dt, order, yt.YT_F32, steps=100)
+    drift = rel_per_quantity(q32, q64).max()
+    assert drift < 1e-4, drift
+    e64 = planewave.l2_error(mesh, N, q64, T, k, 1.0, 2.0, 1.0)
+    e32 = planewave.l2_error(mesh, N, q32, T, k, 1.0, 2.0, 1.0)
+    assert np.allclose(e32, e64, rtol=1e-3)
