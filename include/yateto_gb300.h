@@ -221,6 +221,34 @@ yt_status yt_solver_reference_matrix(const struct yt_solver* solver, const char*
                                      double* out, int64_t* count);
 void yt_solver_destroy(struct yt_solver* solver);
 
+/* ------------------------------------------------------------- p-adaptive batches
+ * Elements of different polynomial degrees in one mesh (orders 2..7 per element; order 7
+ * needs YT_F32).  Each element uses its own degree for derivatives, time integral,
+ * volume and local flux; across a face, the neighbour's face projection is truncated or
+ * zero-padded to the element's face basis (the hierarchical orthogonal basis makes this
+ * the L2 projection).  The elements are grouped by degree; one step is one launch of a
+ * CUDA graph recorded at creation (local kernels of every group, then neighbour kernels
+ * of every group).  DOFs are exchanged in the packed canonical layout: element after
+ * element (in mesh order), each [quantity][basis] with its own B_e = C(o_e + 2, 3). */
+struct yt_batch;
+yt_status yt_batch_create(const yt_mesh_desc* mesh, const int8_t* orders /* host, E */,
+                          const yt_scheme_desc* scheme /* order ignored */, yt_stream stream,
+                          struct yt_batch** out_batch);
+yt_status yt_batch_set_dofs(struct yt_batch* batch, const double* dofs, yt_memory where,
+                            yt_stream stream);
+yt_status yt_batch_get(struct yt_batch* batch, yt_field field, double* out, yt_memory where,
+                       yt_stream stream);
+yt_status yt_batch_step(struct yt_batch* batch, yt_stream stream);
+/* Autotuner: records the step both with the groups in sequence and with the groups on
+ * parallel graph branches, replays each `repeats` times on the current data (the DOFs
+ * are restored afterwards), keeps the faster graph and reports it in *chosen (0
+ * sequential, 1 parallel). Synchronises `stream`. */
+yt_status yt_batch_tune(struct yt_batch* batch, int32_t repeats, yt_stream stream, int32_t* chosen);
+/* Flops and algorithmic device bytes of one step of the whole batch; number of groups. */
+yt_status yt_batch_stats(const struct yt_batch* batch, double* flops, double* bytes,
+                         int32_t* n_groups);
+void yt_batch_destroy(struct yt_batch* batch);
+
 /* Host-only: reference matrices for an order without creating a solver (same meaning as
  * yt_solver_reference_matrix).  Runs no device code. */
 yt_status yt_reference_matrix(int32_t order, const char* name, double* out, int64_t* count);

@@ -201,3 +201,31 @@ def setup_element_matrices(rho, lam, mu, jac):
     star = star_matrices(rho, lam, mu, jac)
     loc, nb = flux_solvers(rho, lam, mu, jac)
     return star, loc, nb
+
+
+def ader_step_mixed(Q_list, orders_n, star, flux_loc, flux_nb, neighbours, faces, orient, dt):
+    """One step of a p-adaptive mesh: element e has degree orders_n[e] and DOFs Q_list[e]
+    (B_e x 9).  The local part is the plain step of degree N_e; the neighbour flux of
+    face s couples B_e test functions with the neighbour's B_nb basis functions through
+    M^-1 F^+ cropped to [B_e, B_nb] (the basis is hierarchical: the first C(n+3,3)
+    functions of any degree span P_n, so the cropped matrix is exactly the integral of
+    the two elements' own functions).  Returns (list of Q_new, list of I)."""
+    E = len(Q_list)
+    I_list = [None] * E
+    out = [None] * E
+    Nmax = int(max(orders_n))
+    m = basis.float_matrices(Nmax)
+    for e in range(E):
+        N = int(orders_n[e])
+        Q = np.asarray(Q_list[e], dtype=np.float64)[None]
+        _, I = derivatives_and_time_integral(Q, star[e:e + 1], dt, N)
+        I_list[e] = I[0]
+        out[e] = local_update(Q, I, star[e:e + 1], flux_loc[e:e + 1], N)[0]
+    for e in range(E):
+        Be = basis.n_basis(int(orders_n[e]))
+        for s in range(4):
+            nb = int(neighbours[e, s])
+            Bn = basis.n_basis(int(orders_n[nb]))
+            F = m['FpHat'][s, faces[e, s], orient[e, s]][:Be, :Bn]
+            out[e] = out[e] + F @ I_list[nb] @ flux_nb[e, s].T
+    return out, I_list

@@ -64,6 +64,13 @@ SIGNATURES = {
                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "yt_solver_reference_matrix": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "yt_solver_destroy": (None, [_P]),
+    "yt_batch_create": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(C.c_int8), C.POINTER(SchemeDesc), _P, C.POINTER(_P)]),
+    "yt_batch_set_dofs": (C.c_int, [_P, _P, C.c_int, _P]),
+    "yt_batch_get": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
+    "yt_batch_step": (C.c_int, [_P, _P]),
+    "yt_batch_tune": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_int32)]),
+    "yt_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "yt_batch_destroy": (None, [_P]),
     "yt_reference_matrix": (C.c_int, [C.c_int32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 

@@ -77,6 +77,15 @@ struct Dims {
   }
 };
 
+// Face projections of the element groups a neighbour may belong to (one group per
+// polynomial degree in a p-adaptive mesh; a single group otherwise): base pointer of the
+// group's [tile][4][9][BT][32] array and its face-basis size BT.
+constexpr int kMaxGroups = 8;
+struct FaceGroups {
+  const void* base[kMaxGroups];
+  int bt[kMaxGroups];
+};
+
 // Global data of the step: the packed non-zero values of the sparse lists, the f^h
 // matrices (3 x BT x BT, column-major f[h][m + n*BT]) and the time-integral weights.
 // The derivatives are carried scaled, D~^d = dt^d D^d: the derivative lists hold
@@ -274,14 +283,18 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restri
 // ------------------------------------------------------------------------- K_neigh
 // Neighbour flux of one tile: dQ += Rhat^s f^h (R^jT I_nb) Anb_s^T, with R^jT I_nb read
 // from the neighbour's face projections written by k_local.
-//   conn : [E_pad][4] packed (neighbour << 4) | (j << 2) | h
+//   conn : [E_pad][4] packed (neighbour << 7) | (group << 4) | (j << 2) | h, the neighbour
+//          index counted within its group; a neighbour whose face basis is smaller
+//          contributes zeros above its size, a larger one is truncated to this degree
+//          (the face basis is hierarchical and orthogonal, so truncation is the L2
+//          projection onto this element's face space)
 // WITH_LOCAL: add the local flux terms Wloc written by k_local<N, false> before lifting,
 // so that Rhat^s is applied once per face to the sum of both flux contributions.
 // The four faces' W (BT x 9 each) stay in shared memory; every row k of Q is then
 // updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
 template <int N, bool WITH_LOCAL, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_neigh(double* Q, const Real* __restrict__ Pface, const Real* __restrict__ Wloc,
+k_neigh(double* Q, FaceGroups G, const Real* __restrict__ Wloc,
         const Real* __restrict__ fnb, const int* __restrict__ conn, StepTables<Real> T) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT;
@@ -297,12 +310,14 @@ k_neigh(double* Q, const Real* __restrict__ Pface, const Real* __restrict__ Wloc
     constexpr int s = decltype(face)::value;
     Real* Xsh = Wsh + s * BT * kNq * kTile;
     const int c = __ldg(conn + e * 4 + s);
-    const size_t nb = (size_t)(c >> 4);
-    const int j = (c >> 2) & 3, h = c & 3;
-    const Real* P = Pface + ((((nb / kTile) * 4 + j) * kNq + w) * BT) * kTile + (nb % kTile);
+    const size_t nb = (size_t)(c >> 7);
+    const int g = (c >> 4) & 7, j = (c >> 2) & 3, h = c & 3;
+    const int btn = G.bt[g];
+    const Real* P = static_cast<const Real*>(G.base[g]) +
+                    ((((nb / kTile) * 4 + j) * kNq + w) * (size_t)btn) * kTile + (nb % kTile);
     Real Pn[BT];
 #pragma unroll
-    for (int n = 0; n < BT; ++n) Pn[n] = __ldg(P + n * kTile);
+    for (int n = 0; n < BT; ++n) Pn[n] = n < btn ? __ldg(P + n * kTile) : Real(0);
     const Real* fh = T.f + (size_t)h * BT * BT;
     // V[m][q] = sum_n f^h_mn Pn[n], f^h block-diagonal by polynomial degree
 #pragma unroll
@@ -356,6 +371,7 @@ struct AderLaunch {
   void *Pface, *Wloc;
   const void *star, *floc, *fnb, *val, *f;
   const int* conn;
+  FaceGroups groups;
   double coeff[8];
   StarPattern SP;
   cudaStream_t stream;
@@ -390,8 +406,7 @@ void ader_launch(const AderLaunch& L) {
         static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP);
   } else {
     k_neigh<N, FUSED, Real><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(
-        L.Q, static_cast<const Real*>(L.Pface), static_cast<const Real*>(L.Wloc),
-        static_cast<const Real*>(L.fnb), L.conn, T);
+        L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T);
   }
 }
 

@@ -231,6 +231,9 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.floc = s->floc_r;
   L.fnb = s->fnb_r;
   L.conn = s->conn;
+  L.groups = FaceGroups{};
+  L.groups.base[0] = s->Pface;
+  L.groups.bt[0] = s->BT;
   const bool f32 = s->prec == YT_F32;
   L.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
   L.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
@@ -378,7 +381,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     YT_REQUIRE(scheme->precision == YT_F32 || scheme->order <= 6, YT_ERR_UNSUPPORTED,
                "YT_F64 solver: orders 2..6 (order 7 needs YT_F32)");
     YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
-    YT_REQUIRE(mesh->n_elements < (int64_t(1) << 27), YT_ERR_UNSUPPORTED, "at most 2^27 elements");
+    YT_REQUIRE(mesh->n_elements < (int64_t(1) << 24), YT_ERR_UNSUPPORTED, "at most 2^24 elements");
     const bool nb = mesh->neighbours != nullptr;
     YT_REQUIRE(!nb || (mesh->faces && mesh->orient), YT_ERR_INVALID, "faces/orient required with neighbours");
     auto s = std::make_unique<yt_solver>();
@@ -401,7 +404,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
           const int j = mesh->faces[e * 4 + f], h = mesh->orient[e * 4 + f];
           YT_REQUIRE(n >= 0 && n < s->E, YT_ERR_INVALID, "neighbour index out of range");
           YT_REQUIRE(j >= 0 && j < 4 && h >= 0 && h < 3, YT_ERR_INVALID, "face/orientation out of range");
-          conn[e * 4 + f] = (int)((n << 4) | (j << 2) | h);
+          conn[e * 4 + f] = (int)((n << 7) | (j << 2) | h);
         }
     }
     build_tables(s.get());
@@ -581,3 +584,323 @@ extern "C" yt_status yt_reference_matrix(int32_t order, const char* name, double
 }
 
 extern "C" void yt_solver_destroy(yt_solver* s) { delete s; }
+
+// ===================================================================== p-adaptive batch
+// Elements of several polynomial degrees: one local-only solver per degree (a "group"),
+// neighbour connectivity across groups, and the whole step recorded once as a CUDA graph
+// (local kernels of all groups, then neighbour kernels of all groups).
+namespace {
+
+__global__ void k_gather_blocked(const double* __restrict__ in, const int64_t* __restrict__ offs,
+                                 double* __restrict__ out, int64_t E, int64_t Epad, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Epad * kNq * B) return;
+  const int lane = (int)(i % kTile);
+  const int64_t rest = i / kTile;
+  const int k = (int)(rest % B);
+  const int q = (int)((rest / B) % kNq);
+  const int64_t e = (rest / ((int64_t)B * kNq)) * kTile + lane;
+  out[i] = e < E ? in[offs[e] + (int64_t)q * B + k] : 0.0;
+}
+__global__ void k_scatter_blocked(const double* __restrict__ in, const int64_t* __restrict__ offs,
+                                  double* __restrict__ out, int64_t E, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * kNq * B) return;
+  const int k = (int)(i % B);
+  const int q = (int)((i / B) % kNq);
+  const int64_t e = i / ((int64_t)B * kNq);
+  out[offs[e] + (int64_t)q * B + k] = in[(((e / kTile) * kNq + q) * B + k) * kTile + (e % kTile)];
+}
+
+}  // namespace
+
+struct yt_batch {
+  yt_precision prec = YT_F64;
+  double dt = 0.0;
+  int64_t E = 0, total_dofs = 0;
+  std::vector<yt_solver*> groups;            // one per degree present
+  std::vector<int> group_n;                  // degree of each group
+  std::vector<std::vector<int64_t>> members; // batch element ids of each group
+  std::vector<int64_t*> d_offs;              // per group: offsets of its elements' DOF blocks
+  std::vector<int*> d_conn;                  // per group: packed cross-group connectivity
+  FaceGroups faces{};
+  double* staging = nullptr;
+  cudaStream_t capture = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  cudaGraphExec_t exec = nullptr;
+  int mode = 0;                              // 0: groups in sequence, 1: groups on parallel branches
+  double flops = 0.0, bytes = 0.0;
+  ~yt_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto* g : groups) delete g;
+    for (auto* p : d_offs) cudaFree(p);
+    for (auto* p : d_conn) cudaFree(p);
+    if (staging) cudaFree(staging);
+    for (auto st : side) cudaStreamDestroy(st);
+    for (auto e : ev) cudaEventDestroy(e);
+    if (capture) cudaStreamDestroy(capture);
+  }
+};
+
+namespace {
+
+AderLaunch batch_launch_args(yt_batch* b, size_t g, cudaStream_t st) {
+  AderLaunch L = launch_args(b->groups[g], st);
+  L.conn = b->d_conn[g];
+  L.groups = b->faces;
+  return L;
+}
+
+void batch_record(yt_batch* b, cudaStream_t st, int mode) {
+  const size_t G = b->groups.size();
+  // (YT_VARIANT_SWITCH dispatches on the degree and precision of the solver named `s`)
+  auto local = [&](size_t g, cudaStream_t stream) {
+    const AderLaunch L = batch_launch_args(b, g, stream);
+    yt_solver* s = b->groups[g];
+    YT_VARIANT_SWITCH(ader_launch, lf, L);
+  };
+  auto neigh = [&](size_t g, cudaStream_t stream) {
+    const AderLaunch L = batch_launch_args(b, g, stream);
+    yt_solver* s = b->groups[g];
+    YT_VARIANT_SWITCH(ader_launch, nf, L);
+  };
+  if (mode == 0) {
+    for (size_t g = 0; g < G; ++g) local(g, st);
+    for (size_t g = 0; g < G; ++g) neigh(g, st);
+    return;
+  }
+  // parallel branches: fork after an event on the capture stream, join before the next phase
+  for (int phase = 0; phase < 2; ++phase) {
+    cuda_check(cudaEventRecord(b->ev[0], st), "fork event");
+    for (size_t g = 0; g < G; ++g) {
+      cuda_check(cudaStreamWaitEvent(b->side[g], b->ev[0], 0), "fork wait");
+      if (phase == 0) local(g, b->side[g]);
+      else neigh(g, b->side[g]);
+      cuda_check(cudaEventRecord(b->ev[1 + g], b->side[g]), "join event");
+      cuda_check(cudaStreamWaitEvent(st, b->ev[1 + g], 0), "join wait");
+    }
+  }
+}
+
+cudaGraphExec_t batch_graph(yt_batch* b, int mode) {
+  cudaGraph_t graph = nullptr;
+  cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    batch_record(b, b->capture, mode);
+  } catch (...) {
+    cudaStreamEndCapture(b->capture, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  cuda_check(cudaStreamEndCapture(b->capture, &graph), "end capture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  cuda_check(e, "graph instantiate");
+  return exec;
+}
+
+}  // namespace
+
+extern "C" yt_status yt_batch_create(const yt_mesh_desc* mesh, const int8_t* orders,
+                                     const yt_scheme_desc* scheme, yt_stream stream,
+                                     yt_batch** out) {
+  return guarded([&] {
+    YT_REQUIRE(mesh && orders && scheme && out, YT_ERR_INVALID, "null argument");
+    *out = nullptr;
+    YT_REQUIRE(mesh->neighbours && mesh->faces && mesh->orient && mesh->material && mesh->jacobian,
+               YT_ERR_INVALID, "a batch needs material, jacobian and full connectivity");
+    YT_REQUIRE(mesh->n_elements > 1 && mesh->n_elements < (int64_t(1) << 24), YT_ERR_INVALID,
+               "element count must be 2 .. 2^24-1");
+    YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
+    auto b = std::make_unique<yt_batch>();
+    b->prec = scheme->precision;
+    b->dt = scheme->dt;
+    b->E = mesh->n_elements;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int> group_of_order(8, -1);
+    std::vector<int> elem_group(b->E);
+    std::vector<int64_t> elem_local(b->E), offs(b->E);
+    for (int64_t e = 0; e < b->E; ++e) {
+      const int o = orders[e];
+      YT_REQUIRE(o >= 2 && o <= 7, YT_ERR_INVALID, "element orders must be 2..7");
+      if (group_of_order[o] < 0) {
+        group_of_order[o] = (int)b->group_n.size();
+        b->group_n.push_back(o - 1);
+        b->members.emplace_back();
+      }
+      const int g = group_of_order[o];
+      elem_group[e] = g;
+      elem_local[e] = (int64_t)b->members[g].size();
+      b->members[g].push_back(e);
+      offs[e] = b->total_dofs;
+      b->total_dofs += (int64_t)kNq * n_basis(o - 1);
+    }
+    YT_REQUIRE(b->group_n.size() <= (size_t)kMaxGroups, YT_ERR_UNSUPPORTED, "too many degrees");
+    for (size_t g = 0; g < b->group_n.size(); ++g) {
+      const auto& mem = b->members[g];
+      std::vector<double> mat(mem.size() * 3), jac(mem.size() * 9);
+      for (size_t i = 0; i < mem.size(); ++i) {
+        std::memcpy(&mat[i * 3], mesh->material + mem[i] * 3, 3 * sizeof(double));
+        std::memcpy(&jac[i * 9], mesh->jacobian + mem[i] * 9, 9 * sizeof(double));
+      }
+      yt_mesh_desc gm{};
+      gm.n_elements = (int64_t)mem.size();
+      gm.material = mat.data();
+      gm.jacobian = jac.data();
+      yt_scheme_desc gs = *scheme;
+      gs.order = b->group_n[g] + 1;
+      yt_solver* sv = nullptr;
+      const yt_status rc = yt_solver_create(&gm, &gs, stream, &sv);
+      if (rc != YT_OK) throw Error(rc, std::string("group of order ") + std::to_string(gs.order) + ": " + yt_last_error());
+      b->groups.push_back(sv);
+      b->faces.base[g] = sv->Pface;
+      b->faces.bt[g] = sv->BT;
+      b->flops += (double)mem.size() * (sv->flops_local + sv->flops_neigh);
+      b->bytes += (double)mem.size() * (sv->bytes_local + sv->bytes_neigh);
+    }
+    for (size_t g = 0; g < b->group_n.size(); ++g) {
+      const auto& mem = b->members[g];
+      yt_solver* sv = b->groups[g];
+      std::vector<int> conn((size_t)sv->Epad * 4, 0);
+      std::vector<int64_t> go(mem.size());
+      for (size_t i = 0; i < mem.size(); ++i) {
+        const int64_t e = mem[i];
+        go[i] = offs[e];
+        for (int f = 0; f < 4; ++f) {
+          const int64_t n = mesh->neighbours[e * 4 + f];
+          const int j = mesh->faces[e * 4 + f], h = mesh->orient[e * 4 + f];
+          YT_REQUIRE(n >= 0 && n < b->E, YT_ERR_INVALID, "neighbour index out of range");
+          YT_REQUIRE(j >= 0 && j < 4 && h >= 0 && h < 3, YT_ERR_INVALID, "face/orientation out of range");
+          conn[i * 4 + f] = (int)((elem_local[n] << 7) | (elem_group[n] << 4) | (j << 2) | h);
+        }
+      }
+      // padding lanes point at element 0 of group 0 with zero flux solvers
+      b->d_conn.push_back(dalloc<int>(conn.size()));
+      cuda_check(cudaMemcpy(b->d_conn.back(), conn.data(), conn.size() * sizeof(int), cudaMemcpyHostToDevice), "copy conn");
+      b->d_offs.push_back(dalloc<int64_t>(go.size()));
+      cuda_check(cudaMemcpy(b->d_offs.back(), go.data(), go.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "copy offsets");
+    }
+    b->staging = dalloc<double>((size_t)b->total_dofs);
+    cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "stream");
+    b->side.resize(b->groups.size());
+    for (auto& s : b->side) cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+    b->ev.resize(b->groups.size() + 1);
+    for (auto& e : b->ev) cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    cuda_check(cudaStreamSynchronize(st), "batch setup");
+    b->exec = batch_graph(b.get(), b->mode);
+    *out = b.release();
+  });
+}
+
+extern "C" yt_status yt_batch_set_dofs(yt_batch* b, const double* dofs, yt_memory where, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(b && dofs, YT_ERR_INVALID, "null argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double* src = dofs;
+    if (where == YT_MEM_HOST) {
+      cuda_check(cudaMemcpyAsync(b->staging, dofs, (size_t)b->total_dofs * sizeof(double), cudaMemcpyHostToDevice, st), "H2D dofs");
+      src = b->staging;
+    } else {
+      YT_REQUIRE(where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
+    }
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+      yt_solver* s = b->groups[g];
+      const int64_t total = s->Epad * kNq * s->B;
+      k_gather_blocked<<<blocks_for(total, 256), 256, 0, st>>>(src, b->d_offs[g], s->Q, s->E, s->Epad, s->B);
+    }
+    cuda_check(cudaGetLastError(), "k_gather_blocked");
+  });
+}
+
+extern "C" yt_status yt_batch_get(yt_batch* b, yt_field field, double* out, yt_memory where, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(b && out, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(field == YT_FIELD_DOFS || field == YT_FIELD_TIME_INTEGRAL, YT_ERR_INVALID, "field");
+    YT_REQUIRE(where == YT_MEM_HOST || where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double* dst = where == YT_MEM_HOST ? b->staging : out;
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+      yt_solver* s = b->groups[g];
+      const int64_t n = s->E * kNq * s->B;
+      k_scatter_blocked<<<blocks_for(n, 256), 256, 0, st>>>(field == YT_FIELD_DOFS ? s->Q : s->I,
+                                                           b->d_offs[g], dst, s->E, s->B);
+    }
+    cuda_check(cudaGetLastError(), "k_scatter_blocked");
+    if (where == YT_MEM_HOST)
+      cuda_check(cudaMemcpyAsync(out, b->staging, (size_t)b->total_dofs * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+  });
+}
+
+extern "C" yt_status yt_batch_step(yt_batch* b, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(b && b->exec, YT_ERR_INVALID, "null batch");
+    cuda_check(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)), "graph launch");
+  });
+}
+
+extern "C" yt_status yt_batch_tune(yt_batch* b, int32_t repeats, yt_stream stream, int32_t* chosen) {
+  return guarded([&] {
+    YT_REQUIRE(b, YT_ERR_INVALID, "null batch");
+    YT_REQUIRE(repeats > 0 && repeats <= 1000, YT_ERR_INVALID, "repeats must be 1..1000");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // time each candidate graph on the caller's data and keep the fastest; the DOFs are
+    // saved before and restored after, so tuning leaves the state unchanged
+    const size_t G = b->groups.size();
+    std::vector<double*> backup(G, nullptr);
+    for (size_t g = 0; g < G; ++g) {
+      yt_solver* s = b->groups[g];
+      const size_t n = (size_t)s->Epad * kNq * s->B;
+      backup[g] = dalloc<double>(n);
+      cuda_check(cudaMemcpyAsync(backup[g], s->Q, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "backup");
+    }
+    cudaEvent_t t0, t1;
+    cuda_check(cudaEventCreate(&t0), "event");
+    cuda_check(cudaEventCreate(&t1), "event");
+    float best = 0.0f;
+    int best_mode = b->mode;
+    for (int mode = 0; mode < 2; ++mode) {
+      cudaGraphExec_t ex = batch_graph(b, mode);
+      cuda_check(cudaGraphLaunch(ex, st), "warm-up");
+      cuda_check(cudaEventRecord(t0, st), "event");
+      for (int r = 0; r < repeats; ++r) cuda_check(cudaGraphLaunch(ex, st), "graph launch");
+      cuda_check(cudaEventRecord(t1, st), "event");
+      cuda_check(cudaEventSynchronize(t1), "sync");
+      float ms = 0.0f;
+      cuda_check(cudaEventElapsedTime(&ms, t0, t1), "elapsed");
+      if (mode == 0 || ms < best) {
+        best = ms;
+        best_mode = mode;
+      }
+      cudaGraphExecDestroy(ex);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (size_t g = 0; g < G; ++g) {
+      yt_solver* s = b->groups[g];
+      const size_t n = (size_t)s->Epad * kNq * s->B;
+      cuda_check(cudaMemcpyAsync(s->Q, backup[g], n * sizeof(double), cudaMemcpyDeviceToDevice, st), "restore");
+    }
+    cuda_check(cudaStreamSynchronize(st), "restore sync");
+    for (auto* p : backup) cudaFree(p);
+    if (best_mode != b->mode) {
+      cudaGraphExec_t ex = batch_graph(b, best_mode);
+      cudaGraphExecDestroy(b->exec);
+      b->exec = ex;
+      b->mode = best_mode;
+    }
+    if (chosen) *chosen = b->mode;
+  });
+}
+
+extern "C" yt_status yt_batch_stats(const yt_batch* b, double* flops, double* bytes, int32_t* n_groups) {
+  return guarded([&] {
+    YT_REQUIRE(b, YT_ERR_INVALID, "null batch");
+    if (flops) *flops = b->flops;
+    if (bytes) *bytes = b->bytes;
+    if (n_groups) *n_groups = (int32_t)b->groups.size();
+  });
+}
+
+extern "C" void yt_batch_destroy(yt_batch* b) { delete b; }

@@ -124,3 +124,84 @@ def reference_matrix(order: int, name: str) -> np.ndarray:
     _lib.check(lib.yt_reference_matrix(order, name.encode(), _ptr(out, C.c_double), C.byref(n)),
                "yt_reference_matrix")
     return out
+
+
+class Batch:
+    """p-adaptive mesh: per-element orders, one CUDA-graph launch per step.
+
+    DOFs are exchanged as a list of (B_e, 9) arrays (the oracle's layout)."""
+
+    def __init__(self, orders, dt, material, jacobian, neighbours, faces, orient,
+                 precision=_lib.YT_F64, stream=None):
+        self.lib = _lib.load()
+        E = int(np.asarray(material).shape[0])
+        self.n_elements = E
+        self.orders = np.ascontiguousarray(orders, dtype=np.int8)
+        self.nb = (self.orders.astype(np.int64) * (self.orders + 1) * (self.orders + 2)) // 6
+        self.offsets = np.concatenate([[0], np.cumsum(9 * self.nb)])
+        self._mat = np.ascontiguousarray(material, dtype=np.float64).reshape(E, 3)
+        self._jac = np.ascontiguousarray(np.asarray(jacobian, dtype=np.float64).reshape(E, 3, 3)
+                                         .transpose(0, 2, 1)).reshape(E, 9)
+        self._nbr = np.ascontiguousarray(neighbours, dtype=np.int32)
+        self._fj = np.ascontiguousarray(faces, dtype=np.int8)
+        self._fh = np.ascontiguousarray(orient, dtype=np.int8)
+        desc = _lib.MeshDesc(n_elements=E, material=_ptr(self._mat, C.c_double),
+                             jacobian=_ptr(self._jac, C.c_double),
+                             neighbours=_ptr(self._nbr, C.c_int32), faces=_ptr(self._fj, C.c_int8),
+                             orient=_ptr(self._fh, C.c_int8))
+        sch = _lib.SchemeDesc(order=0, dt=float(dt), precision=precision, flags=0)
+        handle = C.c_void_p()
+        _lib.check(self.lib.yt_batch_create(C.byref(desc), _ptr(self.orders, C.c_int8), C.byref(sch),
+                                            _stream_handle(stream), C.byref(handle)), "yt_batch_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.yt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, Q_list) -> np.ndarray:
+        return np.concatenate([np.asarray(q, dtype=np.float64).T.ravel() for q in Q_list])
+
+    def unpack(self, flat):
+        return [flat[self.offsets[e]:self.offsets[e + 1]].reshape(9, self.nb[e]).T
+                for e in range(self.n_elements)]
+
+    def set_dofs_host(self, Q_list, stream=None):
+        self._host_in = np.ascontiguousarray(self.pack(Q_list))
+        _lib.check(self.lib.yt_batch_set_dofs(self.handle, self._host_in.ctypes.data, _lib.YT_MEM_HOST,
+                                              _stream_handle(stream)), "yt_batch_set_dofs")
+
+    def set_dofs_ptr(self, ptr, where, stream=None):
+        _lib.check(self.lib.yt_batch_set_dofs(self.handle, ptr, where, _stream_handle(stream)), "yt_batch_set_dofs")
+
+    def get_ptr(self, field, ptr, where, stream=None):
+        _lib.check(self.lib.yt_batch_get(self.handle, field, ptr, where, _stream_handle(stream)), "yt_batch_get")
+
+    def get_host(self, field=_lib.YT_FIELD_DOFS, stream=None):
+        out = np.empty(int(self.offsets[-1]))
+        _lib.check(self.lib.yt_batch_get(self.handle, field, out.ctypes.data, _lib.YT_MEM_HOST,
+                                         _stream_handle(stream)), "yt_batch_get")
+        import torch
+        torch.cuda.synchronize()
+        return self.unpack(out)
+
+    def step(self, stream=None):
+        _lib.check(self.lib.yt_batch_step(self.handle, _stream_handle(stream)), "yt_batch_step")
+
+    def tune(self, repeats=5, stream=None) -> int:
+        chosen = C.c_int32()
+        _lib.check(self.lib.yt_batch_tune(self.handle, repeats, _stream_handle(stream), C.byref(chosen)),
+                   "yt_batch_tune")
+        return chosen.value
+
+    def stats(self):
+        f, b, g = C.c_double(), C.c_double(), C.c_int32()
+        _lib.check(self.lib.yt_batch_stats(self.handle, C.byref(f), C.byref(b), C.byref(g)), "yt_batch_stats")
+        return dict(flops=f.value, bytes=b.value, groups=g.value)

@@ -1,0 +1,96 @@
+"""p-adaptive batches (per-element orders, one CUDA-graph launch per step) against the
+oracle's mixed-order step."""
+import numpy as np
+import pytest
+
+import workload as wl
+from oracle import basis, scheme
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def yt():
+    import paper_1903_11521_gb300 as yt
+    yt.load()
+    return yt
+
+
+def case(E, lo, hi, seed):
+    el = wl.random_elements(E, seed=seed)
+    conn = wl.random_connectivity(E, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    orders = rng.integers(lo, hi + 1, E)
+    Q = [wl.random_dofs(1, basis.n_basis(int(o) - 1), seed=seed + 3 + e, scale="impedance",
+                        elements=wl.Elements(el.rho[e:e + 1], el.lam[e:e + 1], el.mu[e:e + 1],
+                                             el.jac[e:e + 1]))[0] for e, o in enumerate(orders)]
+    dt = wl.cfl_time_step(el, int(orders.max()) - 1)
+    return el, conn, orders, Q, dt
+
+
+def rel(a_list, b_list):
+    a = np.concatenate([x.ravel() for x in a_list])
+    b = np.concatenate([x.ravel() for x in b_list])
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def per_quantity(a_list, b_list):
+    a = np.concatenate(a_list, axis=0)
+    b = np.concatenate(b_list, axis=0)
+    return np.sqrt(((a - b) ** 2).sum(0) / (b ** 2).sum(0))
+
+
+def batch_run(yt, el, conn, orders, Q, dt, precision, steps=1, tune=False):
+    b = yt.Batch(orders, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
+                 conn.faces, conn.orient, precision=precision)
+    b.set_dofs_host(Q)
+    chosen = b.tune(3) if tune else None
+    for _ in range(steps):
+        b.step()
+    q = b.get_host()
+    i = b.get_host(yt.YT_FIELD_TIME_INTEGRAL)
+    st = b.stats()
+    b.close()
+    return q, i, chosen, st
+
+
+def test_mixed_orders_fp64(yt):
+    el, conn, orders, Q, dt = case(150, 2, 6, 50)
+    q, i, _, st = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F64)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
+                                    conn.orient, dt)
+    assert st['groups'] == 5
+    assert per_quantity(i, I).max() < 1e-12
+    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 1e-11
+
+
+def test_mixed_orders_fp32_up_to_order7(yt):
+    el, conn, orders, Q, dt = case(120, 3, 7, 60)
+    q, i, _, _ = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F32)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
+                                    conn.orient, dt)
+    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 2e-5
+
+
+def test_uniform_batch_equals_solver(yt):
+    el, conn, _, _, dt = case(64, 5, 5, 70)
+    Q = wl.random_dofs(64, basis.n_basis(4), seed=71, scale="impedance", elements=el)
+    q, _, _, _ = batch_run(yt, el, conn, np.full(64, 5), list(Q), dt, yt.YT_F64, steps=2)
+    s = yt.Solver(5, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
+                  conn.faces, conn.orient)
+    s.set_dofs_host(Q)
+    s.step()
+    s.step()
+    ref = s.get_host()
+    s.close()
+    assert np.array_equal(np.array(q), ref)
+
+
+def test_tuner_keeps_state_and_result(yt):
+    el, conn, orders, Q, dt = case(200, 3, 6, 80)
+    a, _, chosen, _ = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F64, steps=2, tune=True)
+    b, _, _, _ = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F64, steps=2)
+    assert chosen in (0, 1)
+    assert rel(a, b) < 1e-15
