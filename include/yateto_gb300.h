@@ -249,6 +249,44 @@ yt_status yt_batch_stats(const struct yt_batch* batch, double* flops, double* by
                          int32_t* n_groups);
 void yt_batch_destroy(struct yt_batch* batch);
 
+/* ------------------------------------------------------------------ serving
+ * Independent solves (own mesh, order, dt, DOFs and number of steps) submitted at any
+ * time.  A worker thread admits pending requests in arrival order while the device memory
+ * of the admitted solves fits `hbm_budget_bytes` (a request larger than the whole budget
+ * fails with YT_ERR_OOM), and advances all admitted solves together: each step of the
+ * server runs, per polynomial degree, one local and one neighbour kernel over the tiles
+ * of all admitted solves of that degree, the degrees on separate streams.  A finished
+ * solve is copied out and freed at once, and requests that arrived meanwhile are admitted
+ * as memory frees up.  Results are identical to those of the same solve alone.  The
+ * server uses the device that is current at yt_server_create. */
+typedef struct yt_server_desc {
+  int64_t hbm_budget_bytes;
+  yt_precision precision;    /* YT_F64 (orders 2..6) or YT_F32 (orders 2..7) */
+  int32_t flags;             /* reserved, must be 0 */
+} yt_server_desc;
+
+typedef struct yt_server_stats {
+  int64_t submitted, completed, failed, pending, active, max_active, ticks;
+  int64_t budget_bytes, peak_bytes;  /* peak = most device memory admitted at once */
+  double element_updates;            /* element-steps completed so far */
+} yt_server_stats;
+
+struct yt_server;
+yt_status yt_server_create(const yt_server_desc* desc, struct yt_server** out_server);
+/* Copies the inputs (host memory; DOFs in the canonical layout) and queues the request;
+ * returns at once with its id. */
+yt_status yt_server_submit(struct yt_server* server, const yt_mesh_desc* mesh, int32_t order,
+                           double dt, const double* dofs, int32_t n_steps,
+                           int64_t* request_id);
+/* Blocks until the request is done; copies its final DOFs (canonical layout, host) to
+ * dofs_out unless NULL; latency_s = completion - submission, queue_s = admission -
+ * submission.  Returns the request's error if it failed. */
+yt_status yt_server_wait(struct yt_server* server, int64_t request_id, double* dofs_out,
+                         double* latency_s, double* queue_s);
+yt_status yt_server_stats_get(struct yt_server* server, yt_server_stats* out);
+/* Finishes every submitted request, then stops the worker and frees the server. */
+void yt_server_destroy(struct yt_server* server);
+
 /* Host-only: reference matrices for an order without creating a solver (same meaning as
  * yt_solver_reference_matrix).  Runs no device code. */
 yt_status yt_reference_matrix(int32_t order, const char* name, double* out, int64_t* count);

@@ -8,8 +8,8 @@ package does not load the library; the first call that needs it does, and fails 
 if it has not been built.
 """
 from ._lib import YT_F32, YT_F64, YT_FIELD_DOFS, YT_FIELD_TIME_INTEGRAL, YT_MEM_DEVICE, YT_MEM_HOST, YtError, load
-from .solver import Batch, Solver, reference_matrix
+from .solver import Batch, Server, Solver, reference_matrix
 from .plan import Plan, element_major, from_element_major
 
-__all__ = ["Batch", "Plan", "element_major", "from_element_major", "Solver", "reference_matrix", "load", "YtError", "YT_F64", "YT_F32",
+__all__ = ["Batch", "Server", "Plan", "element_major", "from_element_major", "Solver", "reference_matrix", "load", "YtError", "YT_F64", "YT_F32",
            "YT_MEM_HOST", "YT_MEM_DEVICE", "YT_FIELD_DOFS", "YT_FIELD_TIME_INTEGRAL"]

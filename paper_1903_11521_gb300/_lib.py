@@ -37,6 +37,16 @@ class SchemeDesc(C.Structure):
                 ("flags", C.c_int32)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("precision", C.c_int), ("flags", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "pending", "active",
+                                         "max_active", "ticks", "budget_bytes", "peak_bytes")] + \
+               [("element_updates", C.c_double)]
+
+
 YT_F64, YT_F32 = 0, 1
 YT_MEM_HOST, YT_MEM_DEVICE = 0, 1
 YT_FIELD_DOFS, YT_FIELD_TIME_INTEGRAL = 0, 1
@@ -71,6 +81,12 @@ SIGNATURES = {
     "yt_batch_tune": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "yt_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "yt_batch_destroy": (None, [_P]),
+    "yt_server_create": (C.c_int, [C.POINTER(ServerDesc), C.POINTER(_P)]),
+    "yt_server_submit": (C.c_int, [_P, C.POINTER(MeshDesc), C.c_int32, C.c_double, _P, C.c_int32,
+                                   C.POINTER(C.c_int64)]),
+    "yt_server_wait": (C.c_int, [_P, C.c_int64, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "yt_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "yt_server_destroy": (None, [_P]),
     "yt_reference_matrix": (C.c_int, [C.c_int32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 

@@ -87,16 +87,33 @@ struct FaceGroups {
 };
 
 // Global data of the step: the packed non-zero values of the sparse lists, the f^h
-// matrices (3 x BT x BT, column-major f[h][m + n*BT]) and the time-integral weights.
-// The derivatives are carried scaled, D~^d = dt^d D^d: the derivative lists hold
-// dt Ktilde^x, so D~^{d+1} = sum_x (dt Ktilde^x) D~^d Astar^xT, and the weights are
-// coeff[d] = dt / (d+1)!, which gives I = sum_d dt^{d+1}/(d+1)! D^d.  Magnitudes of D~
+// matrices (3 x BT x BT, column-major f[h][m + n*BT]), the time step and 1/(d+1)!.
+// The derivatives are carried scaled, D~^d = dt^d D^d:
+// D~^{d+1} = dt sum_x Ktilde^x D~^d Astar^xT (the factor dt is applied to each mixed
+// row), and I = sum_d (dt / (d+1)!) D~^d = sum_d dt^{d+1}/(d+1)! D^d.  Magnitudes of D~
 // stay near those of Q (by the CFL condition), which keeps FP32 clear of overflow.
 template <typename Real>
 struct StepTables {
   const Real* val;
   const Real* f;
-  double coeff[8];
+  double dt;
+  double invfact[8];
+};
+
+// One CTA's tile in a launch shared by several independent problems (serving): the
+// problem's buffers, the tile's index within them and the problem's time step.  With a
+// null table a launch covers one problem, tile = blockIdx.x.
+struct TileRef {
+  double* Q;
+  double* I;
+  void* Pface;
+  void* Wloc;
+  const void* star;
+  const void* floc;
+  const void* fnb;
+  const int* conn;
+  int64_t tile;
+  double dt;
 };
 
 // ------------------------------------------------------------------- CK derivatives
@@ -106,7 +123,7 @@ struct StepTables {
 // integral accumulates in double registers; only the C(N+2,3) rows that receive
 // derivative terms need one (rows of degree N hold c0 Q alone).
 template <int N, int DELTA, typename Real>
-__device__ __forceinline__ void ck_step(const StepTables<Real>& T, const int (&scol)[3], int cnt,
+__device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, const int (&scol)[3], int cnt,
                                         Real* __restrict__ Dsh, Real* __restrict__ Xsh,
                                         const Real (&sc)[3][3], double (&Icol)[Dims<N>::nd(1)],
                                         int w, int lane) {
@@ -137,13 +154,14 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, const int (&s
 #pragma unroll
             for (int s = 0; s < 3; ++s)
               if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
+          v *= (Real)dt;
           Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
-          Icol[k0 + kk] = fma(T.coeff[DELTA + 1], (double)v, Icol[k0 + kk]);
+          Icol[k0 + kk] = fma(dt * T.invfact[DELTA + 1], (double)v, Icol[k0 + kk]);
         }
       });
       __syncthreads();
     });
-    ck_step<N, DELTA + 1, Real>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+    ck_step<N, DELTA + 1, Real>(T, dt, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
   }
 }
 
@@ -160,9 +178,8 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, const int (&s
 // LIFT = true applies the local flux here (Q is then the complete local update).
 template <int N, bool LIFT, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restrict__ Pface,
-        Real* __restrict__ Wloc, const Real* __restrict__ star, const Real* __restrict__ floc,
-        StepTables<Real> T, StarPattern SP) {
+k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
+        const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,7 +187,20 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restri
   Real* Xsh = Dsh + B * kNq * kTile;               // XR rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const size_t tile = blockIdx.x;
+  size_t tile = blockIdx.x;
+  double dt = T.dt;
+  if (refs) {
+    const TileRef& r = refs[blockIdx.x];
+    Q = r.Q;
+    Qout = r.Q;
+    Iout = r.I;
+    Pface = static_cast<Real*>(r.Pface);
+    Wloc = static_cast<Real*>(r.Wloc);
+    star = static_cast<const Real*>(r.star);
+    floc = static_cast<const Real*>(r.floc);
+    tile = (size_t)r.tile;
+    dt = r.dt;
+  }
   const double* Qt = Q + tile * (kNq * B * kTile);
 
   // star coefficients of row p = w
@@ -191,16 +221,16 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restri
   for (int k = 0; k < B; ++k) {
     const double q = __ldg(Qt + (w * B + k) * kTile + lane);
     Dsh[(k * kNq + w) * kTile + lane] = (Real)q;
-    if (k < NI) Icol[k < NI ? k : 0] = T.coeff[0] * q;
+    if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
   }
   // (own column only is read before the first barrier)
-  ck_step<N, 0, Real>(T, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+  ck_step<N, 0, Real>(T, dt, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
 
   // publish I: shared (own column) and HBM
   double* It = Iout + tile * (kNq * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    const double ik = k < NI ? Icol[k < NI ? k : 0] : T.coeff[0] * Qt[(w * B + k) * kTile + lane];
+    const double ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
     Dsh[(k * kNq + w) * kTile + lane] = (Real)ik;
     It[(w * B + k) * kTile + lane] = ik;
   }
@@ -294,15 +324,24 @@ k_local(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restri
 // updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
 template <int N, bool WITH_LOCAL, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
-k_neigh(double* Q, FaceGroups G, const Real* __restrict__ Wloc,
-        const Real* __restrict__ fnb, const int* __restrict__ conn, StepTables<Real> T) {
+k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
+        StepTables<Real> T, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Wsh = reinterpret_cast<Real*>(smem_raw);  // 4 faces x BT rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const size_t tile = blockIdx.x;
+  size_t tile = blockIdx.x;
+  if (refs) {
+    const TileRef& r = refs[blockIdx.x];
+    Q = r.Q;
+    Wloc = static_cast<const Real*>(r.Wloc);
+    fnb = static_cast<const Real*>(r.fnb);
+    conn = r.conn;
+    G.base[0] = r.Pface;        // neighbours lie in the same problem (group 0)
+    tile = (size_t)r.tile;
+  }
   const size_t e = tile * kTile + lane;
   const Real* Ft = fnb + tile * (4 * kNq * kNq * kTile);
 
@@ -372,8 +411,9 @@ struct AderLaunch {
   const void *star, *floc, *fnb, *val, *f;
   const int* conn;
   FaceGroups groups;
-  double coeff[8];
+  double dt;
   StarPattern SP;
+  const TileRef* refs;     // null: one problem, grid = ntiles; else grid = ntiles entries
   cudaStream_t stream;
 };
 
@@ -382,7 +422,12 @@ StepTables<Real> step_tables(const AderLaunch& L) {
   StepTables<Real> T;
   T.val = static_cast<const Real*>(L.val);
   T.f = static_cast<const Real*>(L.f);
-  for (int i = 0; i < 8; ++i) T.coeff[i] = L.coeff[i];
+  T.dt = L.dt;
+  double f = 1.0;
+  for (int i = 0; i < 8; ++i) {
+    f *= (i + 1.0);
+    T.invfact[i] = 1.0 / f;
+  }
   return T;
 }
 
@@ -403,10 +448,10 @@ void ader_launch(const AderLaunch& L) {
   if constexpr (LOCAL) {
     k_local<N, !FUSED, Real><<<grid, kNq * kTile, L.smem_local, L.stream>>>(
         L.Q, L.Q, L.I, static_cast<Real*>(L.Pface), static_cast<Real*>(L.Wloc),
-        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP);
+        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP, L.refs);
   } else {
     k_neigh<N, FUSED, Real><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(
-        L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T);
+        L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T, L.refs);
   }
 }
 

@@ -10,6 +10,7 @@
 
 #include "ader_kernels.cuh"
 #include "common.h"
+#include "solver_internal.h"
 #include "tables.h"
 
 using namespace yt;
@@ -186,36 +187,6 @@ T* dalloc(size_t n) {
 
 }  // namespace
 
-struct yt_solver {
-  int N = 0, B = 0, BT = 0;
-  int64_t E = 0, Epad = 0, ntiles = 0;
-  yt_precision prec = YT_F64;
-  double dt = 0.0;
-  bool has_neighbours = false;
-  double *Q = nullptr, *I = nullptr, *star = nullptr, *floc = nullptr, *fnb = nullptr,
-         *staging = nullptr;
-  // buffers of the contraction type (double for YT_F64, float for YT_F32)
-  void *Pface = nullptr, *Wloc = nullptr, *star_r = nullptr, *floc_r = nullptr, *fnb_r = nullptr;
-  int* conn = nullptr;
-  double* d_val = nullptr;
-  double* d_f = nullptr;
-  float* d_val32 = nullptr;
-  float* d_f32 = nullptr;
-  double coeff[8] = {0};
-  size_t real_bytes = 8;
-  double flops_local = 0, flops_neigh = 0, bytes_local = 0, bytes_neigh = 0;
-  double flops_local_unfused = 0;
-  int64_t n_values = 0;
-  size_t smem_local = 0, smem_neigh = 0;
-  ~yt_solver() {
-    if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
-    for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
-                    floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
-                    (void*)d_val32, (void*)d_f32})
-      if (p) cudaFree(p);
-  }
-};
-
 namespace {
 
 AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
@@ -237,7 +208,8 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   const bool f32 = s->prec == YT_F32;
   L.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
   L.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
-  for (int i = 0; i < 8; ++i) L.coeff[i] = s->coeff[i];
+  L.dt = s->dt;
+  L.refs = nullptr;
   L.SP = kStar;
   L.stream = st;
   return L;
@@ -304,12 +276,10 @@ void build_tables(yt_solver* s) {
     const int nin = nd(delta), nout = nd(delta + 1);
     for (int x = 0; x < 3; ++x) {
       const double* K = R.Ktilde.data() + (size_t)x * B * B;
-      // derivatives are carried scaled by dt^delta (D~ = dt^delta D), so the values of the
-      // derivative lists are dt Ktilde: magnitudes stay near those of Q, also in FP32
-      const int off = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; }, s->dt);
+      const int off = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; });
       for (int r = 0; r < nout; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off, r) + 1.0);
     }
-    fl += nout * (2.0 * 3 * kStarSlots + 2.0 * 9);        // mixing + time integral
+    fl += nout * (2.0 * 3 * kStarSlots + 9.0 + 2.0 * 9);  // mixing, dt scaling, time integral
   }
   for (int x = 0; x < 3; ++x) {
     const double* K = R.Khat.data() + (size_t)x * B * B;
@@ -356,16 +326,40 @@ void build_tables(yt_solver* s) {
     cuda_check(cudaMemcpy(s->d_val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy val32");
     cuda_check(cudaMemcpy(s->d_f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy f32");
   }
-  double c = s->dt;
-  for (int d = 0; d <= N && d < 8; ++d) {
-    c /= (d + 1.0);
-    s->coeff[d] = c;        // dt^{d+1}/(d+1)! D^d = dt/(d+1)! D~^d with D~^d = dt^d D^d
-  }
+
 }
 
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
+
+namespace yt {
+AderLaunch solver_launch_args(yt_solver* s, cudaStream_t st) { return launch_args(s, st); }
+
+void solver_launch_variant(yt_solver* s, const AderLaunch& L, int variant) {
+  switch (variant) {
+    case 0: YT_VARIANT_SWITCH(ader_launch, lf, L); break;
+    case 1: YT_VARIANT_SWITCH(ader_launch, ll, L); break;
+    case 2: YT_VARIANT_SWITCH(ader_launch, nf, L); break;
+    case 3: YT_VARIANT_SWITCH(ader_launch, np, L); break;
+    default: throw Error(YT_ERR_INVALID, "kernel variant");
+  }
+  cuda_check(cudaGetLastError(), "kernel launch");
+}
+
+size_t solver_device_bytes(int order, yt_precision prec, int64_t n_elements) {
+  const int N = order - 1;
+  const size_t B = n_basis(N), BT = n_face_basis(N);
+  const size_t Epad = (size_t)((n_elements + kTile - 1) / kTile) * kTile;
+  const size_t rb = prec == YT_F32 ? 4 : 8;
+  size_t per = 8 * kNq * B * 3;                        // Q, I, staging
+  per += 2 * rb * 4 * kNq * BT;                        // face projections, local products
+  per += 8 * (3 * kStarSlots + 8 * 81);                // star matrices, flux solvers
+  if (prec == YT_F32) per += 4 * (3 * kStarSlots + 8 * 81);
+  per += 4 * 4 + 8 * 12;                               // connectivity, setup inputs
+  return Epad * per;
+}
+}  // namespace yt
 
 extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
                                       yt_stream stream, yt_solver** out) {

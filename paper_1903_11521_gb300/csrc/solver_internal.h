@@ -1,0 +1,48 @@
+// Internal view of the solver object, shared by the solver, batch and server code.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/yateto_gb300.h"
+#include "ader_kernels.cuh"
+
+struct yt_solver {
+  int N = 0, B = 0, BT = 0;
+  int64_t E = 0, Epad = 0, ntiles = 0;
+  yt_precision prec = YT_F64;
+  double dt = 0.0;
+  bool has_neighbours = false;
+  double *Q = nullptr, *I = nullptr, *star = nullptr, *floc = nullptr, *fnb = nullptr,
+         *staging = nullptr;
+  // buffers of the contraction type (double for YT_F64, float for YT_F32)
+  void *Pface = nullptr, *Wloc = nullptr, *star_r = nullptr, *floc_r = nullptr, *fnb_r = nullptr;
+  int* conn = nullptr;
+  double* d_val = nullptr;
+  double* d_f = nullptr;
+  float* d_val32 = nullptr;
+  float* d_f32 = nullptr;
+  size_t real_bytes = 8;
+  double flops_local = 0, flops_neigh = 0, bytes_local = 0, bytes_neigh = 0;
+  double flops_local_unfused = 0;
+  int64_t n_values = 0;
+  size_t smem_local = 0, smem_neigh = 0;
+  ~yt_solver() {
+    if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
+    for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
+                    floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
+                    (void*)d_val32, (void*)d_f32})
+      if (p) cudaFree(p);
+  }
+};
+
+
+namespace yt {
+// Launch description of a solver's kernels on `st` (one problem, no tile table).
+AderLaunch solver_launch_args(yt_solver* s, cudaStream_t st);
+// Kernel variant of the solver's degree and precision: 0 local (fused step), 1 local
+// (complete local update), 2 neighbour (fused step), 3 neighbour (after variant 1).
+void solver_launch_variant(yt_solver* s, const AderLaunch& L, int variant);
+// Device bytes a solver of this order / precision / size allocates (its tables aside).
+size_t solver_device_bytes(int order, yt_precision prec, int64_t n_elements);
+}  // namespace yt

@@ -205,3 +205,60 @@ class Batch:
         f, b, g = C.c_double(), C.c_double(), C.c_int32()
         _lib.check(self.lib.yt_batch_stats(self.handle, C.byref(f), C.byref(b), C.byref(g)), "yt_batch_stats")
         return dict(flops=f.value, bytes=b.value, groups=g.value)
+
+
+class Server:
+    """Continuous-batching server of independent solves (see yt_server_* in the C ABI)."""
+
+    def __init__(self, hbm_budget_bytes: int, precision=_lib.YT_F32):
+        self.lib = _lib.load()
+        desc = _lib.ServerDesc(hbm_budget_bytes=int(hbm_budget_bytes), precision=precision, flags=0)
+        handle = C.c_void_p()
+        _lib.check(self.lib.yt_server_create(C.byref(desc), C.byref(handle)), "yt_server_create")
+        self.handle = handle
+        self._shapes = {}
+
+    def submit(self, order, dt, material, jacobian, neighbours, faces, orient, Q, steps) -> int:
+        """Q: numpy (E, B, 9) [element, basis, quantity]; returns the request id."""
+        E = int(np.asarray(material).shape[0])
+        mat = np.ascontiguousarray(material, dtype=np.float64).reshape(E, 3)
+        jac = np.ascontiguousarray(np.asarray(jacobian, dtype=np.float64).reshape(E, 3, 3)
+                                   .transpose(0, 2, 1)).reshape(E, 9)
+        nb = np.ascontiguousarray(neighbours, dtype=np.int32)
+        fj = np.ascontiguousarray(faces, dtype=np.int8)
+        fh = np.ascontiguousarray(orient, dtype=np.int8)
+        canon = np.ascontiguousarray(np.asarray(Q, dtype=np.float64).transpose(0, 2, 1))
+        desc = _lib.MeshDesc(n_elements=E, material=_ptr(mat, C.c_double), jacobian=_ptr(jac, C.c_double),
+                             neighbours=_ptr(nb, C.c_int32), faces=_ptr(fj, C.c_int8),
+                             orient=_ptr(fh, C.c_int8))
+        rid = C.c_int64()
+        _lib.check(self.lib.yt_server_submit(self.handle, C.byref(desc), int(order), float(dt),
+                                             canon.ctypes.data, int(steps), C.byref(rid)),
+                   "yt_server_submit")
+        self._shapes[rid.value] = (E, canon.shape[2])
+        return rid.value
+
+    def wait(self, rid: int):
+        """(Q (E, B, 9), latency s, queue s)."""
+        E, B = self._shapes[rid]
+        out = np.empty((E, 9, B))
+        lat, q = C.c_double(), C.c_double()
+        _lib.check(self.lib.yt_server_wait(self.handle, rid, out.ctypes.data, C.byref(lat), C.byref(q)),
+                   "yt_server_wait")
+        return out.transpose(0, 2, 1), lat.value, q.value
+
+    def stats(self) -> dict:
+        st = _lib.ServerStats()
+        _lib.check(self.lib.yt_server_stats_get(self.handle, C.byref(st)), "yt_server_stats_get")
+        return {n: getattr(st, n) for n, _ in _lib.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.yt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
