@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision, batching and serving measurements")
     return ap.parse_args()
 
 
@@ -207,6 +209,138 @@ def oracle_rate(order, target_s=12.0, workers=None):
     return n2 / t, n2, t, workers
 
 
+# ------------------------------------------------------------------------ forms
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _increment_error(yt, order, precision, n=20000):
+    """Max over quantities of the relative Frobenius error of Q_new - Q against the FP64
+    path (itself equal to the oracle to 1e-12) after one step on n elements."""
+    N = order - 1
+    B = order * (order + 1) * (order + 2) // 6
+    el = wl.random_elements(n, seed=77)
+    conn = wl.random_connectivity(n, seed=78)
+    Q = wl.random_dofs(n, B, seed=79, scale="impedance", elements=el)
+    dt = wl.cfl_time_step(el, N)
+    mat = np.stack([el.rho, el.lam, el.mu], 1)
+    out = []
+    for prec in (yt.YT_F64, precision):
+        s = yt.Solver(order, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient, precision=prec)
+        s.set_dofs_host(Q)
+        s.step()
+        out.append(s.get_host() - Q)
+        s.close()
+    num = np.sqrt(((out[1] - out[0]) ** 2).sum((0, 1)))
+    return float((num / np.sqrt((out[0] ** 2).sum((0, 1)))).max())
+
+
+def form_precision(yt, order, E, steps, stream):
+    N = order - 1
+    B = order * (order + 1) * (order + 2) // 6
+    el = wl.random_elements(E, seed=wl.SEED + 500)
+    conn = wl.random_connectivity(E, seed=wl.SEED + 502)
+    Q = wl.random_dofs(E, B, seed=wl.SEED + 501)
+    dt = wl.cfl_time_step(el, N)
+    s = yt.Solver(order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
+                  conn.faces, conn.orient, precision=yt.YT_F32, stream=stream)
+    s.set_dofs_host(Q, stream=stream)
+    ms = _timed(lambda: s.step(stream=stream), steps, 2, stream)
+    s.close()
+    out = {"workload": f"order {order}, {E} tets, FP32 contractions / FP64 setup, accumulation and DOFs",
+           "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms}
+    if order <= 6:
+        out["error_vs_fp64_increment"] = _increment_error(yt, order, yt.YT_F32)
+        out["error_definition"] = ("max over quantities of ||dQ_f32 - dQ_f64||_F / ||dQ_f64||_F, "
+                                   "one step, 20000 tets, against the FP64 path")
+    else:
+        out["error_bound"] = ("order 7 has no FP64 path; the parity tests bound the FP32 increment "
+                              "error against the FP64 oracle by 2e-5 per quantity")
+    return out
+
+
+def form_batching(yt, E, precision, lo, hi, steps, stream):
+    rng = np.random.default_rng(wl.SEED + 600)
+    orders = rng.integers(lo, hi + 1, E).astype(np.int8)
+    el = wl.random_elements(E, seed=wl.SEED + 601)
+    conn = wl.random_connectivity(E, seed=wl.SEED + 602)
+    dt = wl.cfl_time_step(el, int(orders.max()) - 1)
+    b = yt.Batch(orders, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
+                 conn.faces, conn.orient, precision=precision, stream=stream)
+    flat = rng.standard_normal(int(b.offsets[-1]))
+    b._host_in = flat
+    b.set_dofs_ptr(flat.ctypes.data, yt.YT_MEM_HOST, stream=stream)
+    chosen = b.tune(3, stream=stream)
+    ms = _timed(lambda: b.step(stream=stream), steps, 2, stream)
+    st = b.stats()
+    b.close()
+    return {"workload": f"p-adaptive mesh, {E} tets, per-element order U{{{lo}..{hi}}}, "
+                        f"{'FP32' if precision == yt.YT_F32 else 'FP64'}",
+            "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms,
+            "graph": "one CUDA graph launch per step; tuner chose "
+                     + ("parallel branches" if chosen == 1 else "groups in sequence"),
+            "groups": st["groups"], "achieved_tflops": st["flops"] / (ms / 1e3) / 1e12}
+
+
+def form_serving(yt, n_requests=256, rate=20.0, steps=100, budget=64 << 30):
+    import threading as th
+    rng = np.random.default_rng(wl.SEED + 700)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_requests)).astype(int)
+    orders = rng.integers(3, 7, n_requests)
+    reqs = []
+    for i in range(n_requests):
+        E, o = int(sizes[i]), int(orders[i])
+        el = wl.random_elements(E, seed=wl.SEED + 10000 + 3 * i)
+        conn = wl.random_connectivity(E, seed=wl.SEED + 10001 + 3 * i)
+        Q = np.random.default_rng(wl.SEED + 10002 + 3 * i).standard_normal(
+            (E, o * (o + 1) * (o + 2) // 6, 9))
+        reqs.append((o, wl.cfl_time_step(el, o - 1), np.stack([el.rho, el.lam, el.mu], 1), el.jac,
+                     conn.neighbours, conn.faces, conn.orient, Q))
+    srv = yt.Server(budget, precision=yt.YT_F32)
+    ids = [None] * n_requests
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(*r, steps)
+
+    thread = th.Thread(target=submitter)
+    thread.start()
+    thread.join()
+    lat, queue = [], []
+    for rid in ids:
+        _, l, q = srv.wait(rid)
+        lat.append(l)
+        queue.append(q)
+    t_end = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat) * 1e3
+    return {"workload": f"{n_requests} independent elastic solves, Poisson arrivals {rate}/s, "
+                        f"sizes log-U[1e3, 2e5] tets, orders U{{3..6}}, {steps} steps each, FP32 "
+                        f"contractions / FP64 accumulation, HBM budget {budget >> 30} GiB",
+            "solves_per_s": n_requests / t_end, "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)),
+            "p50_queue_ms": float(np.percentile(np.array(queue) * 1e3, 50)),
+            "element_updates_per_s": st["element_updates"] / t_end,
+            "makespan_s": t_end, "max_active": st["max_active"], "peak_bytes": st["peak_bytes"],
+            "completed": st["completed"], "failed": st["failed"]}
+
+
 # ------------------------------------------------------------------------ GPU bench
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -333,11 +467,20 @@ def run_ours(args):
         cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
                "sample": f"{n_s} elements of the same workload recipe, one full step "
                          f"({t_s:.1f} s), dense unfactorised FP64 oracle"}
+    forms = None
+    if not args.no_forms and ws == 1:
+        forms = {"precision_o6": form_precision(yt, 6, E, 5, stream),
+                 "precision_o7": form_precision(yt, 7, E, 5, stream),
+                 "batching_fp32": form_batching(yt, 2 * E, yt.YT_F32, 3, 7, 5, stream),
+                 "batching_fp64": form_batching(yt, 2 * E, yt.YT_F64, 3, 6, 3, stream),
+                 "serving": form_serving(yt)}
+        forms["batching_fp64"]["note"] = ("orders 3..6: an order-7 FP64 tile needs 258 KB of shared "
+                                          "memory, above the 227 KB of one CTA")
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
-            "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
             "gpu_launches": 2 * K,
             "kernel_ms": {"k_local": local_ms, "k_neigh": neigh_ms},
             "context": {"paper_skx_dp_o6_element_updates_per_s": 1244e6 / (56 * 9),
