@@ -38,6 +38,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak derived from the unit counts and clocks of the part: 152 SMs x 2 FP64 FMA
 # per clock per SM x 2 flop x 2070 MHz = 1.2586 TFLOP/s (nominal FP64: 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 FMA peak from the same unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
 NCU_TRAFFIC_PER_ELEMENT = {"a22a8529d82d5fcb": {6: (297.324800e6 + 746.231040e6) / 40000}}
@@ -60,6 +62,8 @@ def parse():
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
+                    help="contraction type of the main measurement (default FP64)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batching and serving measurements")
     return ap.parse_args()
@@ -70,7 +74,7 @@ def workload_config(args, extra=None):
                        f"(B={(args.order) * (args.order + 1) * (args.order + 2) // 6} x 9 quantities), "
                        f"{args.elements} tets, random 4-regular face matching",
            "order": args.order, "elements": args.elements, "quantities": 9,
-           "precision": "fp64", "seed": wl.SEED,
+           "precision": args.precision, "seed": wl.SEED,
            "l2": "per-step working set (Q, I, face projections: ~14 GB) exceeds the 129 MB L2"}
     if extra:
         cfg.update(extra)
@@ -367,8 +371,9 @@ def run_ours(args):
     Q = wl.random_dofs(E, B, seed=seed + 1)
     dt = wl.cfl_time_step(el, N)
     stream = torch.cuda.current_stream()
+    prec = yt.YT_F32 if args.precision == "f32" else yt.YT_F64
     solver = yt.Solver(args.order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac,
-                       conn.neighbours, conn.faces, conn.orient, stream=stream)
+                       conn.neighbours, conn.faces, conn.orient, precision=prec, stream=stream)
     solver.set_dofs_host(Q, stream=stream)
     torch.cuda.synchronize()
     stats = solver.stats()
@@ -446,18 +451,21 @@ def run_ours(args):
 
     flops_local = stats["local_flops"] * E
     achieved = flops_local / (local_ms / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS if args.precision == "f32" else FP64_PEAK_TFLOPS
+    peak_source = ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)" if args.precision == "f32"
+                   else "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)")
     roofline = {"bound": "alu", "kernel": "k_local (derivatives + time integral + volume + face projections + local flux products)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": peak_source,
                 "traffic": None,
-                "k_neigh_frac": stats["neighbour_flops"] * E / (neigh_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                "step_frac": (stats["local_flops"] + stats["neighbour_flops"]) * E / (total_ms / K / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                "k_neigh_frac": stats["neighbour_flops"] * E / (neigh_ms / 1e3) / 1e12 / peak,
+                "step_frac": (stats["local_flops"] + stats["neighbour_flops"]) * E / (total_ms / K / 1e3) / 1e12 / peak,
                 "flops_per_element": {"local": stats["local_flops"], "neighbour": stats["neighbour_flops"]}}
     # DRAM bytes per element of k_local from one ncu capture of a 40,000-tet case, valid
     # only for the kernel source it was taken on (scaled to E: traffic grows with E)
     digest = kernel_source_digest()
-    if args.order in NCU_TRAFFIC_PER_ELEMENT.get(digest, {}):
+    if args.precision == "f64" and args.order in NCU_TRAFFIC_PER_ELEMENT.get(digest, {}):
         roofline["traffic"] = NCU_TRAFFIC_PER_ELEMENT[digest][args.order] * E
         roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, scaled)"
 
@@ -478,7 +486,7 @@ def run_ours(args):
                                           "memory, above the 227 KB of one CTA")
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
             "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
             "gpu_launches": 2 * K,

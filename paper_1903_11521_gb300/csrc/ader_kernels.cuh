@@ -79,7 +79,7 @@ struct Dims {
 
 // Face projections of the element groups a neighbour may belong to (one group per
 // polynomial degree in a p-adaptive mesh; a single group otherwise): base pointer of the
-// group's [tile][4][9][BT][32] array and its face-basis size BT.
+// group's [element][4][9][BT] array and its face-basis size BT.
 constexpr int kMaxGroups = 8;
 struct FaceGroups {
   const void* base[kMaxGroups];
@@ -169,7 +169,9 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
 // Derivatives, time integral, volume and local flux of one tile of 32 elements.
 //   Q, Qout : [tile][9][B][32] double   (may alias)
 //   Iout    : [tile][9][B][32] double
-//   Pface   : [tile][4][9][BT][32]      projections R^sT I of the four faces
+//   Pface   : [element][4][9][BT]       projections R^sT I of the four faces, contiguous per
+//                                       element so that a neighbour's face block is read
+//                                       whole (the only per-element array gathered at random)
 //   star    : [tile][3][24][32]         non-zero slots of Astar^x
 //   floc    : [tile][4][9][9][32]       local flux solvers (row p, column q)
 //   Wloc    : [tile][4][9][BT][32]      (R^sT I) Aloc_s^T per face, written when LIFT is
@@ -270,7 +272,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   });
 
   // local flux: dQ += Rhat^s ((R^sT I) Aloc_s^T)
-  Real* Pt = Pface + tile * (4 * kNq * BT * kTile);
+  Real* Pt = Pface + (tile * kTile + lane) * (4 * kNq * BT);
   const Real* Ft = floc + tile * (4 * kNq * kNq * kTile);
   static_for<0, 4>([&](auto face) {
     constexpr int s = decltype(face)::value;
@@ -278,7 +280,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
       constexpr int m = decltype(mm)::value;
       const Real z = gen::Row<N, 21 + s, m>::dot(T.val, icol);
       Xsh[(m * kNq + w) * kTile + lane] = z;
-      Pt[((s * kNq + w) * BT + m) * kTile + lane] = z;
+      Pt[(s * kNq + w) * BT + m] = z;
     });
     Real a[kNq];
 #pragma unroll
@@ -309,6 +311,21 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   });
 
 }
+
+// ------------------------------------------------------------- asynchronous copies
+// Global -> shared copy of one element (4 or 8 bytes) that bypasses the registers
+// (cp.async), grouped and waited for per face.
+template <typename Real>
+__device__ __forceinline__ void cp_async_elem(Real* dst_shared, const Real* src_global) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(dst_shared);
+  if constexpr (sizeof(Real) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src_global) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src_global) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
 
 // ------------------------------------------------------------------------- K_neigh
 // Neighbour flux of one tile: dQ += Rhat^s f^h (R^jT I_nb) Anb_s^T, with R^jT I_nb read
@@ -345,18 +362,38 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   const size_t e = tile * kTile + lane;
   const Real* Ft = fnb + tile * (4 * kNq * kNq * kTile);
 
+  // The neighbour's projection for face s is copied asynchronously into this thread's
+  // column of face s's slot of Wsh (free until face s is processed); the copy for face
+  // s + 1 is issued before face s is computed, so the gather overlaps computation.
+  auto prefetch = [&](auto face) {
+    constexpr int s = decltype(face)::value;
+    const int c = __ldg(conn + e * 4 + s);
+    const size_t nb = (size_t)(c >> 7);
+    const int g = (c >> 4) & 7, j = (c >> 2) & 3;
+    const int btn = G.bt[g];
+    const Real* P = static_cast<const Real*>(G.base[g]) + ((nb * 4 + j) * kNq + w) * (size_t)btn;
+    Real* dst = Wsh + s * BT * kNq * kTile + w * kTile + lane;
+#pragma unroll
+    for (int n = 0; n < BT; ++n) {
+      if (n < btn) cp_async_elem(dst + n * kNq * kTile, P + n);
+      else dst[n * kNq * kTile] = Real(0);
+    }
+    cp_async_commit();
+  };
+  prefetch(std::integral_constant<int, 0>{});
   static_for<0, 4>([&](auto face) {
     constexpr int s = decltype(face)::value;
     Real* Xsh = Wsh + s * BT * kNq * kTile;
-    const int c = __ldg(conn + e * 4 + s);
-    const size_t nb = (size_t)(c >> 7);
-    const int g = (c >> 4) & 7, j = (c >> 2) & 3, h = c & 3;
-    const int btn = G.bt[g];
-    const Real* P = static_cast<const Real*>(G.base[g]) +
-                    ((((nb / kTile) * 4 + j) * kNq + w) * (size_t)btn) * kTile + (nb % kTile);
+    const int h = __ldg(conn + e * 4 + s) & 3;
+    if constexpr (s < 3) {
+      prefetch(std::integral_constant<int, s + 1>{});
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     Real Pn[BT];
 #pragma unroll
-    for (int n = 0; n < BT; ++n) Pn[n] = n < btn ? __ldg(P + n * kTile) : Real(0);
+    for (int n = 0; n < BT; ++n) Pn[n] = Xsh[(n * kNq + w) * kTile + lane];
     const Real* fh = T.f + (size_t)h * BT * BT;
     // V[m][q] = sum_n f^h_mn Pn[n], f^h block-diagonal by polynomial degree
 #pragma unroll
