@@ -92,8 +92,15 @@ def lists(N, B, BT, Kt, Kh, R, Rh):
     return out, off
 
 
-def emit_rows(N, lst):
+CONST_MAX_N = 5          # FP32 values of degrees <= 5 fit the 64 KB constant bank
+
+
+def emit_rows(N, lst, nvals):
     lines = []
+    if N <= CONST_MAX_N:
+        # FP32 values in constant memory: each non-zero becomes one fma with a
+        # constant-bank operand (one copy per translation unit, uploaded by the solver)
+        lines.append(f"static __constant__ float c_vals_o{N}[{max(nvals, 1)}];")
     for list_id, rows in lst:
         for r, row in enumerate(rows):
             lines.append(f"template <> struct Row<{N}, {list_id}, {r}> {{")
@@ -115,6 +122,23 @@ def emit_rows(N, lst):
                              for i in range(0, len(terms), 2)]
                 lines.append(f"    return {terms[0]};")
             lines.append("  }")
+            if N <= CONST_MAX_N:
+                lines.append("  static __device__ __forceinline__ float dotc(const float* __restrict__ x) {")
+                if not row:
+                    lines.append("    return 0.0f;")
+                else:
+                    na = min(N_ACC, len(row))
+                    for a in range(na):
+                        lines.append(f"    float a{a} = 0.0f;")
+                    for i, (c, voff) in enumerate(row):
+                        a = i % na
+                        lines.append(f"    a{a} = fmaf(c_vals_o{N}[{voff}], x[{c * ROW_STRIDE}], a{a});")
+                    terms = [f"a{a}" for a in range(na)]
+                    while len(terms) > 1:
+                        terms = [f"({terms[i]} + {terms[i + 1]})" if i + 1 < len(terms) else terms[i]
+                                 for i in range(0, len(terms), 2)]
+                    lines.append(f"    return {terms[0]};")
+                lines.append("  }")
             lines.append("};")
     return "\n".join(lines) + "\n"
 
@@ -130,6 +154,7 @@ UNIT = """// Generated by codegen.py: one kernel variant ({V}) of polynomial deg
 namespace yt {{
 void ader_set_attribute_o{N}_{P}_{V}(size_t smem) {{ ader_set_attribute<{N}, {REAL}, {LOCAL}, {FUSED}>(smem); }}
 void ader_launch_o{N}_{P}_{V}(const AderLaunch& L) {{ ader_launch<{N}, {REAL}, {LOCAL}, {FUSED}>(L); }}
+int ader_upload_o{N}_{P}_{V}(const float* vals, size_t n) {{ {UPLOAD} }}
 }}  // namespace yt
 """
 
@@ -160,12 +185,16 @@ def generate(build_dir: str) -> list[str]:
         counts[N] = nvals
         header = (f"// Generated by codegen.py: unrolled sparse rows of polynomial degree {N} "
                   f"({nvals} non-zeros).\n#pragma once\nnamespace yt {{\nnamespace gen {{\n"
-                  + emit_rows(N, lst) + "}  // namespace gen\n}  // namespace yt\n")
+                  + emit_rows(N, lst, nvals) + "}  // namespace gen\n}  // namespace yt\n")
         _write_if_changed(os.path.join(gen, f"yt_rows_o{N}.cuh"), header)
     for N, P in UNITS:
         for V, (local, fused) in VARIANTS.items():
             unit = os.path.join(gen, f"ader_o{N}_{P}_{V}.cu")
-            _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused,
+            if P == "f32" and N <= CONST_MAX_N:
+                upload = (f"return (int)cudaMemcpyToSymbol(gen::c_vals_o{N}, vals, n * sizeof(float));")
+            else:
+                upload = "(void)vals; (void)n; return 0;"
+            _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused, UPLOAD=upload,
                                                 REAL="double" if P == "f64" else "float"))
             units.append(unit)
     info = os.path.join(gen, "ader_gen_info.cu")

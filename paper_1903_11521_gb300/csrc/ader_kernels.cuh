@@ -46,6 +46,16 @@ template <int N, int LIST, int ROW>
 struct Row;
 }  // namespace gen
 
+// Sparse row of a list: FP32 values of degrees <= 5 come from constant memory
+// (Row::dotc, one constant-bank operand per fma), otherwise from the value array.
+template <int N, int LIST, int ROW, typename Real>
+__device__ __forceinline__ Real row_dot(const Real* __restrict__ v, const Real* __restrict__ x) {
+  if constexpr (sizeof(Real) == 4 && N <= 5)
+    return gen::Row<N, LIST, ROW>::dotc(x);
+  else
+    return gen::Row<N, LIST, ROW>::dot(v, x);
+}
+
 template <int Begin, int End, typename F>
 __device__ __forceinline__ void static_for(F&& f) {
   if constexpr (Begin < End) {
@@ -138,9 +148,9 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
       static_for<0, KC>([&](auto kkc) {
         constexpr int kk = decltype(kkc)::value;
         if constexpr (k0 + kk < nout) {
-          Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 0, k0 + kk>::dot(T.val, xcol);
-          Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 1, k0 + kk>::dot(T.val, xcol);
-          Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, DELTA * 3 + 2, k0 + kk>::dot(T.val, xcol);
+          Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 0, k0 + kk>(T.val, xcol);
+          Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 1, k0 + kk>(T.val, xcol);
+          Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 2, k0 + kk>(T.val, xcol);
         }
       });
       __syncthreads();
@@ -249,9 +259,9 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
     static_for<0, KC>([&](auto kkc) {
       constexpr int kk = decltype(kkc)::value;
       if constexpr (k0 + kk < B) {
-        Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 18, k0 + kk>::dot(T.val, icol);
-        Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 19, k0 + kk>::dot(T.val, icol);
-        Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = gen::Row<N, 20, k0 + kk>::dot(T.val, icol);
+        Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 18, k0 + kk>(T.val, icol);
+        Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 19, k0 + kk>(T.val, icol);
+        Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 20, k0 + kk>(T.val, icol);
       }
     });
     __syncthreads();
@@ -278,7 +288,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
     constexpr int s = decltype(face)::value;
     static_for<0, BT>([&](auto mm) {
       constexpr int m = decltype(mm)::value;
-      const Real z = gen::Row<N, 21 + s, m>::dot(T.val, icol);
+      const Real z = row_dot<N, 21 + s, m>(T.val, icol);
       Xsh[(m * kNq + w) * kTile + lane] = z;
       Pt[(s * kNq + w) * BT + m] = z;
     });
@@ -301,7 +311,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
       const Real* wcol = Xsh + w * kTile + lane;
       static_for<0, B>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        Qo[(w * B + k) * kTile + lane] += (double)gen::Row<N, 25 + s, k>::dot(T.val, wcol);
+        Qo[(w * B + k) * kTile + lane] += (double)row_dot<N, 25 + s, k>(T.val, wcol);
       });
     } else {
       Real* Wt = Wloc + tile * (4 * kNq * BT * kTile);
@@ -429,10 +439,10 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   static_for<0, B>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     const Real* wcol = Wsh + w * kTile + lane;
-    double dq = (double)gen::Row<N, 25, k>::dot(T.val, wcol);
-    dq += (double)gen::Row<N, 26, k>::dot(T.val, wcol + 1 * BT * kNq * kTile);
-    dq += (double)gen::Row<N, 27, k>::dot(T.val, wcol + 2 * BT * kNq * kTile);
-    dq += (double)gen::Row<N, 28, k>::dot(T.val, wcol + 3 * BT * kNq * kTile);
+    double dq = (double)row_dot<N, 25, k>(T.val, wcol);
+    dq += (double)row_dot<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile);
+    dq += (double)row_dot<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile);
+    dq += (double)row_dot<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile);
     Qt[(w * B + k) * kTile + lane] += dq;
   });
 }
@@ -498,7 +508,8 @@ void ader_launch(const AderLaunch& L) {
 // shared-memory footprint (258 KB) exceeds the 227 KB a CTA may use.
 #define YT_DECLARE_ADER_VARIANT(N, P, V)                  \
   void ader_set_attribute_o##N##_##P##_##V(size_t);      \
-  void ader_launch_o##N##_##P##_##V(const AderLaunch&);
+  void ader_launch_o##N##_##P##_##V(const AderLaunch&);  \
+  int ader_upload_o##N##_##P##_##V(const float*, size_t);
 #define YT_DECLARE_ADER_UNIT(N, P)     \
   YT_DECLARE_ADER_VARIANT(N, P, lf)    \
   YT_DECLARE_ADER_VARIANT(N, P, ll)    \

@@ -321,6 +321,16 @@ void build_tables(yt_solver* s) {
   cuda_check(cudaMemcpy(s->d_f, R.f.data(), R.f.size() * sizeof(double), cudaMemcpyHostToDevice), "copy f");
   if (s->prec == YT_F32) {
     std::vector<float> v32(csr.val.begin(), csr.val.end()), f32(R.f.begin(), R.f.end());
+    // FP32 values of degrees <= 5 are also read from constant memory (one copy per kernel
+    // variant's translation unit)
+    if (N <= 5) {
+      int rc = 0;
+      YT_VARIANT_SWITCH(rc |= ader_upload, lf, v32.data(), v32.size());
+      YT_VARIANT_SWITCH(rc |= ader_upload, ll, v32.data(), v32.size());
+      YT_VARIANT_SWITCH(rc |= ader_upload, nf, v32.data(), v32.size());
+      YT_VARIANT_SWITCH(rc |= ader_upload, np, v32.data(), v32.size());
+      YT_REQUIRE(rc == 0, YT_ERR_CUDA, "upload of constant values failed");
+    }
     s->d_val32 = dalloc<float>(v32.size());
     s->d_f32 = dalloc<float>(f32.size());
     cuda_check(cudaMemcpy(s->d_val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy val32");
