@@ -6,7 +6,8 @@ face matching with random orientations, DOFs ~ N(0,1)).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  `value` is device-resident throughput (inputs in HBM);
-`e2e` runs the same step through the C ABI with host buffers (H2D of Q, step, D2H of Q).
+`e2e` runs the same step through the C ABI with pinned host buffers (yt_step_host: H2D of
+Q, step, D2H of Q, the copies pipelined with the kernels in element chunks).
 `--impl reference` times the FP64 oracle on the host cores on a bounded sample.
 Under torchrun (N > 1) every rank solves its own independent problem of the same size
 (weak scaling, no data-path collective); the timed region is bracketed by barriers and the
@@ -42,13 +43,20 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"a22a8529d82d5fcb": {6: (297.324800e6 + 746.231040e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"6363f0fb7c3ca347": {6: (304.142592e6 + 753.175040e6) / 40000}}
 
 
-def kernel_source_digest():
+def kernel_source_digest(order=6, precision="f64"):
+    """Digest of what the timed kernels of one order and contraction type are built from:
+    the kernel header and the generated rows and units of that degree."""
     h = hashlib.sha256()
-    for rel in ("csrc/ader_kernels.cuh", "codegen.py"):
-        h.update(open(os.path.join(ROOT, "paper_1903_11521_gb300", rel), "rb").read())
+    n = order - 1
+    pkg = os.path.join(ROOT, "paper_1903_11521_gb300")
+    files = [os.path.join(pkg, "csrc", "ader_kernels.cuh"),
+             os.path.join(pkg, "_build", "gen", f"yt_rows_o{n}.cuh")]
+    files += [os.path.join(pkg, "_build", "gen", f"ader_o{n}_{precision}_{v}.cu") for v in ("lf", "nf")]
+    for f in files:
+        h.update(open(f, "rb").read() if os.path.exists(f) else b"missing")
     return h.hexdigest()[:16]
 
 
@@ -62,7 +70,7 @@ def parse():
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16x3"],
                     help="contraction type of the main measurement (default FP64)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batching and serving measurements")
@@ -249,23 +257,33 @@ def _increment_error(yt, order, precision, n=20000):
     return float((num / np.sqrt((out[0] ** 2).sum((0, 1)))).max())
 
 
-def form_precision(yt, order, E, steps, stream):
+PRECISION_NAMES = {"f64": "FP64", "f32": "FP32", "bf16x3": "split-BF16 tensor-core (hi+lo, 3 products, FP32 accumulation)"}
+
+
+def precision_code(yt, name):
+    return {"f64": yt.YT_F64, "f32": yt.YT_F32, "bf16x3": yt.YT_BF16X3_F32ACC}[name]
+
+
+def form_precision(yt, order, E, steps, stream, precision="f32"):
     N = order - 1
     B = order * (order + 1) * (order + 2) // 6
     el = wl.random_elements(E, seed=wl.SEED + 500)
     conn = wl.random_connectivity(E, seed=wl.SEED + 502)
     Q = wl.random_dofs(E, B, seed=wl.SEED + 501)
     dt = wl.cfl_time_step(el, N)
+    code = precision_code(yt, precision)
     s = yt.Solver(order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
-                  conn.faces, conn.orient, precision=yt.YT_F32, stream=stream)
+                  conn.faces, conn.orient, precision=code, stream=stream)
     s.set_dofs_host(Q, stream=stream)
     ms = _timed(lambda: s.step(stream=stream), steps, 2, stream)
+    s.status(stream=stream)
     s.close()
-    out = {"workload": f"order {order}, {E} tets, FP32 contractions / FP64 setup, accumulation and DOFs",
+    out = {"workload": f"order {order}, {E} tets, {PRECISION_NAMES[precision]} contractions / "
+                       f"FP64 setup, accumulation and DOFs",
            "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms}
     if order <= 6:
-        out["error_vs_fp64_increment"] = _increment_error(yt, order, yt.YT_F32)
-        out["error_definition"] = ("max over quantities of ||dQ_f32 - dQ_f64||_F / ||dQ_f64||_F, "
+        out["error_vs_fp64_increment"] = _increment_error(yt, order, code)
+        out["error_definition"] = ("max over quantities of ||dQ - dQ_f64||_F / ||dQ_f64||_F, "
                                    "one step, 20000 tets, against the FP64 path")
     else:
         out["error_bound"] = ("order 7 has no FP64 path; the parity tests bound the FP32 increment "
@@ -371,7 +389,7 @@ def run_ours(args):
     Q = wl.random_dofs(E, B, seed=seed + 1)
     dt = wl.cfl_time_step(el, N)
     stream = torch.cuda.current_stream()
-    prec = yt.YT_F32 if args.precision == "f32" else yt.YT_F64
+    prec = precision_code(yt, args.precision)
     solver = yt.Solver(args.order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac,
                        conn.neighbours, conn.faces, conn.orient, precision=prec, stream=stream)
     solver.set_dofs_host(Q, stream=stream)
@@ -418,16 +436,12 @@ def run_ours(args):
         canon.numpy()[:] = Q.transpose(0, 2, 1)
         out = torch.empty_like(canon, pin_memory=True)
         for _ in range(2):
-            solver.set_dofs_ptr(canon.data_ptr(), yt.YT_MEM_HOST, stream=stream)
-            solver.step(stream=stream)
-            solver.get_ptr(yt.YT_FIELD_DOFS, out.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+            solver.step_host_ptr(canon.data_ptr(), out.data_ptr(), stream=stream)
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(K):
-            solver.set_dofs_ptr(canon.data_ptr(), yt.YT_MEM_HOST, stream=stream)
-            solver.step(stream=stream)
-            solver.get_ptr(yt.YT_FIELD_DOFS, out.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+            solver.step_host_ptr(canon.data_ptr(), out.data_ptr(), stream=stream)
         b.record(stream)
         barrier()
         e_ms = a.elapsed_time(b)
@@ -451,8 +465,8 @@ def run_ours(args):
 
     flops_local = stats["local_flops"] * E
     achieved = flops_local / (local_ms / 1e3) / 1e12
-    peak = FP32_PEAK_TFLOPS if args.precision == "f32" else FP64_PEAK_TFLOPS
-    peak_source = ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)" if args.precision == "f32"
+    peak = FP32_PEAK_TFLOPS if args.precision != "f64" else FP64_PEAK_TFLOPS
+    peak_source = ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)" if args.precision != "f64"
                    else "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)")
     roofline = {"bound": "alu", "kernel": "k_local (derivatives + time integral + volume + face projections + local flux products)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -464,7 +478,7 @@ def run_ours(args):
                 "flops_per_element": {"local": stats["local_flops"], "neighbour": stats["neighbour_flops"]}}
     # DRAM bytes per element of k_local from one ncu capture of a 40,000-tet case, valid
     # only for the kernel source it was taken on (scaled to E: traffic grows with E)
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(args.order, args.precision)
     if args.precision == "f64" and args.order in NCU_TRAFFIC_PER_ELEMENT.get(digest, {}):
         roofline["traffic"] = NCU_TRAFFIC_PER_ELEMENT[digest][args.order] * E
         roofline["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, scaled)"
@@ -478,6 +492,7 @@ def run_ours(args):
     forms = None
     if not args.no_forms and ws == 1:
         forms = {"precision_o6": form_precision(yt, 6, E, 5, stream),
+                 "precision_o6_bf16x3": form_precision(yt, 6, E, 5, stream, "bf16x3"),
                  "precision_o7": form_precision(yt, 7, E, 5, stream),
                  "batching_fp32": form_batching(yt, 2 * E, yt.YT_F32, 3, 7, 5, stream),
                  "batching_fp64": form_batching(yt, 2 * E, yt.YT_F64, 3, 6, 3, stream),

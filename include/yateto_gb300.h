@@ -51,7 +51,11 @@ typedef enum yt_status {
 typedef enum yt_precision {
   YT_F64 = 0,              /* all arithmetic in binary64 */
   YT_F32 = 1,              /* bulk contractions in binary32, setup in binary64 */
-  YT_BF16X3_F32ACC = 2     /* reserved: split-bf16 tensor-core contractions */
+  YT_BF16X3_F32ACC = 2     /* products with the global matrices on the tensor cores: each
+                              operand split into two bfloat16 parts (hi + lo), three
+                              products hi*hi + hi*lo + lo*hi accumulated in binary32;
+                              per-element 9x9 products in binary32, DOFs and time-integral
+                              accumulation in binary64 (solver only, orders 2..6) */
 } yt_precision;
 
 typedef enum yt_memory { YT_MEM_HOST = 0, YT_MEM_DEVICE = 1 } yt_memory;
@@ -176,7 +180,7 @@ typedef struct yt_mesh_desc {
 typedef struct yt_scheme_desc {
   int32_t order;             /* convergence order O = N + 1; this build: 2..6 */
   double dt;                 /* time step */
-  yt_precision precision;    /* YT_F64 or YT_F32 */
+  yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7), YT_BF16X3_F32ACC (2..6) */
   int32_t flags;             /* reserved, must be 0 */
 } yt_scheme_desc;
 
@@ -209,11 +213,28 @@ yt_status yt_step_neighbour(struct yt_solver* solver, yt_stream stream);
  * products (R^sT I) Aloc_s^T; phase 1 adds the neighbour products and applies
  * Rhat^s once per face to their sum.  Q is only consistent after phase 1. */
 yt_status yt_step_phase(struct yt_solver* solver, int32_t phase, yt_stream stream);
+/* One step (as yt_step) on host buffers: Q is read from `dofs_in` and the new Q written to
+ * `dofs_out` (host memory, canonical layout; they may be the same buffer).  The transfers
+ * are pipelined with the kernels in 8 element chunks on an internal copy stream: the
+ * upload of a chunk overlaps the local kernel of the previous one, and the download of a
+ * chunk overlaps the neighbour kernel of the next one (the neighbour kernel of any chunk
+ * needs the local results of all chunks).  Host buffers should be pinned for the copies
+ * to run asynchronously.  Asynchronous on `stream`: the step, including the last
+ * download, is complete when `stream` reaches this point.  The time integral stays on
+ * the device (yt_solver_get). */
+yt_status yt_step_host(struct yt_solver* solver, const double* dofs_in, double* dofs_out,
+                       yt_stream stream);
 /* Flops per element executed by the two phases of yt_step, and their algorithmic device
  * bytes per element (each stream read or written once). */
 yt_status yt_solver_stats(const struct yt_solver* solver, double* local_flops,
                           double* neighbour_flops, double* local_bytes,
                           double* neighbour_bytes);
+/* Synchronises `stream`, then reports whether a bounded device-side wait of this solver's
+ * kernels ran out since the last call: the tensor-core kernels (YT_BF16X3_F32ACC) wait on
+ * tensor-core completion with a limit of one second and then stop with their outputs
+ * incomplete.  Returns YT_ERR_TIMEOUT (and clears the record) in that case, else YT_OK.
+ * No counterpart in the paper: a safeguard of this implementation. */
+yt_status yt_solver_status(struct yt_solver* solver, yt_stream stream);
 /* Reference matrix `name` ("M", "Khat", "Ktilde", "R", "Rhat", "f") of this solver's
  * order as double, column-major, stacked over its first index (3, 4 or 3 matrices);
  * `count` receives the number of doubles; pass out == NULL to query the size. */

@@ -47,7 +47,7 @@ class ServerStats(C.Structure):
                [("element_updates", C.c_double)]
 
 
-YT_F64, YT_F32 = 0, 1
+YT_F64, YT_F32, YT_BF16X3_F32ACC = 0, 1, 2
 YT_MEM_HOST, YT_MEM_DEVICE = 0, 1
 YT_FIELD_DOFS, YT_FIELD_TIME_INTEGRAL = 0, 1
 
@@ -70,8 +70,10 @@ SIGNATURES = {
     "yt_step_local": (C.c_int, [_P, _P]),
     "yt_step_neighbour": (C.c_int, [_P, _P]),
     "yt_step_phase": (C.c_int, [_P, C.c_int32, _P]),
+    "yt_step_host": (C.c_int, [_P, _P, _P, _P]),
     "yt_solver_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "yt_solver_status": (C.c_int, [_P, _P]),
     "yt_solver_reference_matrix": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "yt_solver_destroy": (None, [_P]),
     "yt_batch_create": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(C.c_int8), C.POINTER(SchemeDesc), _P, C.POINTER(_P)]),

@@ -1,0 +1,755 @@
+// Tensor-core form of the ADER-DG step (precision YT_BF16X3_F32ACC): the products with
+// the global matrices (CK derivatives Ktilde^x, volume Khat^x, face projections R^sT,
+// lifting Rhat^s; Sec. 5.1.1 of the paper) run on the 5th-generation tensor cores as
+// element-batched GEMMs, the per-element 9x9 products (star matrices, flux solvers) and
+// the time-integral accumulation stay on the CUDA cores.
+//
+// Split precision.  Each operand value x is carried as two bfloat16 numbers,
+// x_hi = bf16(x) and x_lo = bf16(x - x_hi) (together 16 significant bits), and a product
+// a x is formed from the three tensor-core products a_hi x_hi + a_hi x_lo + a_lo x_hi
+// with FP32 accumulation in tensor memory (the dropped a_lo x_lo term is below 2^-16 of
+// |a x|).  The global matrices are split once on the host; element data are split by
+// the threads that produce them.
+//
+// GEMM orientation.  For a tile of 32 elements, the M dimension is the (quantity,
+// element) pair: the element operand has 288 rows r(q, e) and K = basis functions; the
+// global matrix (transposed) is the N x K operand with N = output basis functions.  The
+// 288 rows form three M = 128 groups: quantities 0-3 (rows 32..159), 4-7 (rows
+// 160..287) and quantity 8 (rows 0..31; the group's rows 32..127 overlap the first group
+// and give accumulator lanes that are never read).  Thread (warp q, lane e) therefore
+// writes its own operand row and reads its own accumulator lane: warp q's TMEM lane
+// quarter is q mod 4, which is where row (q, e) of its group lands.
+//
+// Shared-memory operands use the K-major, unswizzled canonical layout: 8 x 8 bf16 core
+// matrices of 128 contiguous bytes (a row's 8 K-consecutive values in 16 bytes),
+// K-adjacent core matrices 128 bytes apart, groups of 8 rows kp * 16 bytes apart.
+//
+// Synchronisation.  One elected thread issues the MMAs of a pass and commits them to an
+// mbarrier; all threads wait for it (bounded, see tc_wait) before reading the
+// accumulators with tcgen05.ld.  Every device-side wait gives up after kTcWaitNs and
+// reports YT_ERR_TIMEOUT through the status word; the kernel then issues no further MMA,
+// finishes its tile, waits (bounded) for what it issued and frees its tensor memory.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ader_kernels.cuh"
+
+namespace yt {
+namespace tc {
+
+constexpr int kRows = kNq * kTile;                 // 288 element-operand rows
+constexpr unsigned long long kTcWaitNs = 1000000000ull;   // 1 s
+constexpr int kStatusTimeout = 7;                  // YT_ERR_TIMEOUT
+
+__host__ __device__ constexpr int up8(int x) { return (x + 7) / 8 * 8; }
+__host__ __device__ constexpr int up16(int x) { return (x + 15) / 16 * 16; }
+__host__ __device__ constexpr int max2(int a, int b) { return a > b ? a : b; }
+
+// Byte offset of entry (row r, k) of a canonical operand with K capacity kp.
+__host__ __device__ constexpr int op_offset(int r, int k, int kp) {
+  return (r / 8) * (kp * 16) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+}
+// Element-operand row of (quantity q, element e) and first row of each M = 128 group.
+__host__ __device__ constexpr int op_row(int q, int e) { return q == 8 ? e : 32 + 32 * q + e; }
+__host__ __device__ constexpr int group_first_row(int g) { return g == 0 ? 32 : (g == 1 ? 160 : 0); }
+__host__ __device__ constexpr int group_of(int q) { return q < 4 ? 0 : (q < 8 ? 1 : 2); }
+
+// Passes of the two kernels of degree N.  A pass is one set of MMAs into the three
+// accumulator groups (N columns each, K = kp): k_local runs CK derivatives delta = 0..N-1
+// (columns x * R8 + k, R = C(N-delta+2,3) output rows), NV volume passes over row chunks
+// (columns x * R8 + k - k0) and the face projections (columns s * BT8 + m); k_neigh runs
+// one lifting pass (columns k, K = s * BT8 + m).
+template <int N>
+__host__ __device__ constexpr int tc_nv() {
+  int n = 1;
+  while (up16(3 * up8((Dims<N>::B + n - 1) / n)) > 160) ++n;
+  return n;
+}
+template <int N>
+__host__ __device__ constexpr int tc_vr() { return up8((Dims<N>::B + tc_nv<N>() - 1) / tc_nv<N>()); }
+template <int N>
+__host__ __device__ constexpr int tc_vrows(int v) {
+  return (Dims<N>::B - v * tc_vr<N>()) < tc_vr<N>() ? (Dims<N>::B - v * tc_vr<N>()) : tc_vr<N>();
+}
+template <int N>
+__host__ __device__ constexpr int tc_r8(int p) {
+  return p < N ? up8(Dims<N>::nd(p + 1)) : (p < N + tc_nv<N>() ? up8(tc_vrows<N>(p - N)) : up8(Dims<N>::BT));
+}
+template <int N>
+__host__ __device__ constexpr int tc_np(int p) {
+  return p < N + tc_nv<N>() ? up16(3 * tc_r8<N>(p)) : up16(4 * up8(Dims<N>::BT));
+}
+template <int N>
+__host__ __device__ constexpr int tc_kp(int p) {
+  return p < N ? up16(Dims<N>::nd(p)) : (p < N + tc_nv<N>() ? up16(Dims<N>::nd(1)) : up16(Dims<N>::B));
+}
+template <int N>
+__host__ __device__ constexpr int tc_off(int p) {
+  return p == 0 ? 0 : tc_off<N>(p - 1) + 2 * tc_np<N>(p - 1) * tc_kp<N>(p - 1) * 2;
+}
+template <int N>
+__host__ __device__ constexpr int tc_cs() {
+  int c = 0;
+  for (int p = 0; p < N + tc_nv<N>() + 1; ++p) c = max2(c, tc_np<N>(p));
+  return c;
+}
+
+template <int N>
+struct Layout {
+  using D = Dims<N>;
+  static constexpr int B = D::B, BT = D::BT, BT8 = up8(BT), NI = D::nd(1);
+  static constexpr int KPA = up16(B);                  // K capacity, k_local element operand
+  static constexpr int NV = tc_nv<N>();
+  static constexpr int VR = tc_vr<N>();               // rows per volume pass
+  static constexpr int NPASS = N + NV + 1;
+  __host__ __device__ static constexpr int vrows(int v) { return tc_vrows<N>(v); }
+  __host__ __device__ static constexpr int r8(int p) { return tc_r8<N>(p); }
+  __host__ __device__ static constexpr int np(int p) { return tc_np<N>(p); }
+  __host__ __device__ static constexpr int kp(int p) { return tc_kp<N>(p); }
+  __host__ __device__ static constexpr int off(int p) { return tc_off<N>(p); }
+  static constexpr int BLOB = tc_off<N>(NPASS);
+  static constexpr int CS = tc_cs<N>();               // TMEM columns per group
+  static constexpr int OPA_SPLIT = kRows * KPA * 2;    // bytes of one split
+  static constexpr int XS_FLOATS = 3 * kNq * 2 * kTile * 4;
+  static constexpr size_t SMEM = (size_t)2 * OPA_SPLIT + BLOB + XS_FLOATS * 4 + 64;
+  // k_neigh
+  static constexpr int KPN = up16(4 * BT8);
+  static constexpr int NPL = up16(B);
+  static constexpr int OPN_SPLIT = kRows * KPN * 2;
+  static constexpr int BLOB_N = 2 * NPL * KPN * 2;
+  static constexpr int STAGE_FLOATS = BT * kNq * kTile;      // one face of gathered projections
+  static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 2 * STAGE_FLOATS * 4 + 64;
+  static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
+  static_assert(BT8 / 8 <= 3, "face basis too large for the exchange buffer");
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Shared-memory matrix descriptor: start, LBO = 128 (K-adjacent core matrices), SBO
+// (row-group stride), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 accumulator,
+// M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Generic-proxy shared-memory writes become visible to the tensor cores (async proxy).
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk (TMA) copy global -> shared, completion counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity` of `bar`: false after kTcWaitNs.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  while (global_timer() - t0 < kTcWaitNs)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+// 8 consecutive FP32 accumulator columns of this thread's lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&r)[8]) {
+  uint32_t u[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tmem_ld3x8(uint32_t a0, uint32_t a1, uint32_t a2, float (&r)[3][8]) {
+  uint32_t u[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23])
+      : "r"(a0), "r"(a1), "r"(a2)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 24; ++i) r[i / 8][i % 8] = __uint_as_float(u[i]);
+}
+
+// Stores 8 K-consecutive values of one operand row as hi and lo bf16 parts.
+__device__ __forceinline__ void store_split8(unsigned char* op, int split_bytes, int off, const float (&v)[8]) {
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+    lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  *reinterpret_cast<uint4*>(op + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(op + split_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// The MMAs of one pass (elected thread): three groups x K steps of 16 x three products.
+__device__ __forceinline__ void issue_pass(uint32_t tmem, int cs, uint32_t a_base, int a_split, int kpa,
+                                           uint32_t b_base, int np, int kp, uint32_t bar) {
+  const uint32_t idesc = idesc_bf16(np);
+  const uint32_t sbo_a = (uint32_t)kpa * 16, sbo_b = (uint32_t)kp * 16;
+  const uint32_t b_lo = b_base + (uint32_t)(np * kp * 2);
+  for (int g = 0; g < 3; ++g) {
+    const uint32_t a_hi = a_base + (uint32_t)(group_first_row(g) / 8) * sbo_a;
+    const uint32_t a_lo = a_hi + (uint32_t)a_split;
+    const uint32_t d = tmem + (uint32_t)(g * cs);
+    for (int j = 0; j < kp / 16; ++j) {
+      const uint32_t dk = (uint32_t)j * 256;
+      mma_bf16(d, smem_desc(a_hi + dk, sbo_a), smem_desc(b_base + dk, sbo_b), idesc, j > 0);
+      mma_bf16(d, smem_desc(a_hi + dk, sbo_a), smem_desc(b_lo + dk, sbo_b), idesc, 1);
+      mma_bf16(d, smem_desc(a_lo + dk, sbo_a), smem_desc(b_base + dk, sbo_b), idesc, 1);
+    }
+  }
+  mma_commit(bar);
+}
+
+struct TcStep {
+  double dt;
+  double invfact[8];
+};
+
+// Per-CTA resources: tensor memory, two mbarriers (operand load, MMA completion).
+struct TcShared {
+  uint64_t bar[2];
+  uint32_t tmem;
+  int ok;
+};
+
+// Allocation of `ncols` tensor-memory columns by warp 0 (written to ts->tmem).
+template <int NCOLS>
+__device__ __forceinline__ void tmem_alloc(TcShared* ts) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ts->tmem)),
+               "n"(NCOLS)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+template <int NCOLS>
+__device__ __forceinline__ void tmem_free(uint32_t tmem) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS) : "memory");
+}
+
+// Loads `bytes` of pre-split global-matrix operands into shared memory with bulk copies
+// (elected thread; chunks of at most 32 KB, all counted on bar).
+__device__ __forceinline__ void load_operands(unsigned char* dst, const unsigned char* src, int bytes,
+                                              uint32_t bar) {
+  mbar_expect_tx(bar, (uint32_t)bytes);
+  for (int o = 0; o < bytes; o += 32768) {
+    const int n = bytes - o < 32768 ? bytes - o : 32768;
+    bulk_load(smem_u32(dst + o), src + o, (uint32_t)n, bar);
+  }
+}
+
+// ------------------------------------------------------------------------- K_local
+// Derivatives, time integral, volume, face projections and local flux products of tiles
+// of 32 elements; persistent CTAs (grid <= number of tiles) stride over the tiles.
+// Outputs and layouts as k_local<N, false, float>: Q (volume added), I, Pface
+// [element][4][9][BT], Wloc [tile][4][9][BT][32] = (R^sT I) Aloc_s^T.
+template <int N>
+__global__ void __launch_bounds__(kRows, 1)
+k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, float* __restrict__ Wloc,
+           const float* __restrict__ star, const float* __restrict__ floc,
+           const unsigned char* __restrict__ blob, TcStep T, StarPattern SP, int64_t ntiles,
+           int* __restrict__ status) {
+  using L = Layout<N>;
+  using Dm = Dims<N>;
+  constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPA = L::KPA, NI = L::NI, CS = L::CS, NV = L::NV;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPA
+  unsigned char* opb = opa + 2 * L::OPA_SPLIT;                    // global-matrix passes
+  float* xs = reinterpret_cast<float*>(opb + L::BLOB);            // [3][9][2][32][4]
+  TcShared* ts = reinterpret_cast<TcShared*>(xs + L::XS_FLOATS);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool leader = threadIdx.x == 0;
+  const uint32_t bar_ld = smem_u32(&ts->bar[0]), bar_mma = smem_u32(&ts->bar[1]);
+
+  // zero the element operand once: padding columns are read (times zero) by every pass
+  for (int i = threadIdx.x; i < 2 * L::OPA_SPLIT / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(opa)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (w == 0) tmem_alloc<512>(ts);
+  if (leader) {
+    mbar_init(bar_ld, 1);
+    mbar_init(bar_mma, 1);
+    mbar_fence_init();
+  }
+  fence_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = ts->tmem;
+  if (leader) load_operands(opb, blob, L::BLOB, bar_ld);
+  bool ok = __syncthreads_and(tc_wait(bar_ld, 0)) != 0;
+  uint32_t phase = 0;
+  bool pending = false;              // a commit whose wait timed out
+  uint32_t pending_phase = 0;
+
+  const uint32_t opa_s = smem_u32(opa), opb_s = smem_u32(opb);
+  const int g = group_of(w);
+  const uint32_t my_tmem = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(g * CS);
+  const int my_row = op_row(w, lane);
+  const int s0 = SP.start[w], cnt = SP.start[w + 1] - s0;
+  int scol[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) scol[s] = (s < cnt) ? SP.col[s0 + s] : 0;
+  const double dt = T.dt;
+
+  // MMAs are issued only while ok (block-uniform), so every issued pass is waited for
+  auto issue = [&](int p) {
+    if (leader && ok) {
+      fence_after_sync();
+      issue_pass(tmem, CS, opa_s, L::OPA_SPLIT, KPA, opb_s + (uint32_t)L::off(p), L::np(p), L::kp(p), bar_mma);
+    }
+  };
+  auto wait_pass = [&]() {
+    const bool was_ok = ok;
+    const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
+    ok = __syncthreads_and(done) != 0;
+    if (was_ok && !ok) {
+      pending = true;
+      pending_phase = phase;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+  };
+  // publishes this thread's operand writes and TMEM reads before the next MMA issue
+  auto sync_for_mma = [&]() {
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+  };
+  // star product of an 8-row chunk held in xs: v[i] = sum_x sum_q Astar^x_pq X^x[k0+i][q]
+  auto mix_star = [&](const float (&sc)[3][3], float (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        if (s < cnt) {
+          const float4* src = reinterpret_cast<const float4*>(xs) + ((x * kNq + scol[s]) * 2) * kTile + lane;
+          const float4 a = src[0], b = src[kTile];
+          const float c = sc[x][s];
+          v[0] = fmaf(c, a.x, v[0]);
+          v[1] = fmaf(c, a.y, v[1]);
+          v[2] = fmaf(c, a.z, v[2]);
+          v[3] = fmaf(c, a.w, v[3]);
+          v[4] = fmaf(c, b.x, v[4]);
+          v[5] = fmaf(c, b.y, v[5]);
+          v[6] = fmaf(c, b.z, v[6]);
+          v[7] = fmaf(c, b.w, v[7]);
+        }
+  };
+  // 3 x 8 accumulator columns (plane stride r8) of this thread's lane into xs
+  auto stage_chunk = [&](int col0, int r8) {
+    float r[3][8];
+    tmem_ld3x8(my_tmem + col0, my_tmem + col0 + r8, my_tmem + col0 + 2 * r8, r);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      float4* dst = reinterpret_cast<float4*>(xs) + ((x * kNq + w) * 2) * kTile + lane;
+      dst[0] = make_float4(r[x][0], r[x][1], r[x][2], r[x][3]);
+      dst[kTile] = make_float4(r[x][4], r[x][5], r[x][6], r[x][7]);
+    }
+  };
+
+  for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    const double* Qt = Q + tile * (kNq * B * kTile);
+    double* Qo = Q + tile * (kNq * B * kTile);
+    float sc[3][3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : 0.0f;
+
+    // D~^0 = Q as operand; I starts as dt Q
+    double Icol[NI];
+    static_for<0, up8(B) / 8>([&](auto cc) {
+      constexpr int k0 = decltype(cc)::value * 8;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = k0 + i;
+        const double q = k < B ? __ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0;
+        if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
+        v[i] = (float)q;
+      }
+      store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+    });
+    sync_for_mma();
+    issue(0);
+
+    // CK derivatives: D~^{delta+1} = dt sum_x (Ktilde^x D~^delta) Astar^xT, in the operand
+    static_for<0, N>([&](auto dd) {
+      constexpr int DELTA = decltype(dd)::value;
+      constexpr int R = Dm::nd(DELTA + 1), R8 = up8(R);
+      wait_pass();
+      static_for<0, R8 / 8>([&](auto cc) {
+        constexpr int k0 = decltype(cc)::value * 8;
+        stage_chunk(k0, R8);
+        __syncthreads();
+        float v[8];
+        mix_star(sc, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = k0 + i;
+          if (k < R) {
+            v[i] *= (float)dt;
+            Icol[k < NI ? k : 0] = fma(dt * T.invfact[DELTA + 1], (double)v[i], Icol[k < NI ? k : 0]);
+          } else {
+            v[i] = 0.0f;
+          }
+        }
+        store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+        sync_for_mma();
+      });
+      if constexpr (DELTA + 1 < N) issue(DELTA + 1);
+    });
+
+    // time integral: HBM (double) and operand
+    double* It = Iout + tile * (kNq * B * kTile);
+    static_for<0, up8(B) / 8>([&](auto cc) {
+      constexpr int k0 = decltype(cc)::value * 8;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = k0 + i;
+        if (k < B) {
+          const double ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+          It[(w * B + k) * kTile + lane] = ik;
+          v[i] = (float)ik;
+        } else {
+          v[i] = 0.0f;
+        }
+      }
+      store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+    });
+    sync_for_mma();
+    issue(N);
+
+    // volume: Q[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q], row chunks of VR
+    static_for<0, NV>([&](auto vv) {
+      constexpr int V = decltype(vv)::value;
+      constexpr int R = L::vrows(V), R8 = up8(R), KB0 = V * L::VR;
+      wait_pass();
+      static_for<0, R8 / 8>([&](auto cc) {
+        constexpr int k0 = decltype(cc)::value * 8;
+        stage_chunk(k0, R8);
+        __syncthreads();
+        float v[8];
+        mix_star(sc, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = KB0 + k0 + i;
+          if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + (double)v[i];
+        }
+        fence_before_sync();
+        __syncthreads();
+      });
+      if constexpr (V + 1 < NV) issue(N + V + 1);
+      else issue(N + NV);
+    });
+
+    // face projections P^s = R^sT I -> Pface; local flux products W = P^s Aloc_s^T -> Wloc
+    wait_pass();
+    float* Pe = Pface + (tile * kTile + lane) * (4 * kNq * BT);
+    const float* Ft = floc + tile * (4 * kNq * kNq * kTile);
+    float* Wt = Wloc + tile * (4 * kNq * BT * kTile);
+    static_for<0, 4>([&](auto face) {
+      constexpr int s = decltype(face)::value;
+      static_for<0, BT8 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        float r[8];
+        tmem_ld8(my_tmem + s * BT8 + 8 * c, r);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (8 * c + i < BT) Pe[(s * kNq + w) * BT + 8 * c + i] = r[i];
+        float4* dst = reinterpret_cast<float4*>(xs) + ((c * kNq + w) * 2) * kTile + lane;
+        dst[0] = make_float4(r[0], r[1], r[2], r[3]);
+        dst[kTile] = make_float4(r[4], r[5], r[6], r[7]);
+      });
+      float a[kNq];
+#pragma unroll
+      for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
+      __syncthreads();
+      static_for<0, BT8 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kNq; ++q) {
+          const float4* src = reinterpret_cast<const float4*>(xs) + ((c * kNq + q) * 2) * kTile + lane;
+          const float4 x0 = src[0], x1 = src[kTile];
+          v[0] = fmaf(a[q], x0.x, v[0]);
+          v[1] = fmaf(a[q], x0.y, v[1]);
+          v[2] = fmaf(a[q], x0.z, v[2]);
+          v[3] = fmaf(a[q], x0.w, v[3]);
+          v[4] = fmaf(a[q], x1.x, v[4]);
+          v[5] = fmaf(a[q], x1.y, v[5]);
+          v[6] = fmaf(a[q], x1.z, v[6]);
+          v[7] = fmaf(a[q], x1.w, v[7]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (8 * c + i < BT) Wt[((s * kNq + w) * BT + 8 * c + i) * kTile + lane] = v[i];
+      });
+      fence_before_sync();
+      __syncthreads();
+    });
+  }
+  // after a timeout: one more bounded wait for the pass in flight, then free
+  if (pending) (void)tc_wait(bar_mma, pending_phase);
+  if (!ok && leader) atomicExch(status, kStatusTimeout);
+  fence_before_sync();
+  __syncthreads();
+  if (w == 0) {
+    fence_after_sync();
+    tmem_free<512>(tmem);
+  }
+}
+
+// ------------------------------------------------------------------------- K_neigh
+// Flux lifting of tiles of 32 elements: W^s = [Wloc^s] + [f^h (R^jT I_nb) Anb_s^T] per
+// face (CUDA cores, as k_neigh<N, ..., float>), then Q += sum_s Rhat^s W^s as one
+// tensor-core pass with K = the four faces' W stacked (s * BT8 + m).
+//   WITH_LOCAL: add the local flux products written by k_local_tc
+//   WITH_NEIGH: add the neighbour contributions (gathered face projections)
+template <int N, bool WITH_LOCAL, bool WITH_NEIGH>
+__global__ void __launch_bounds__(kRows, 1)
+k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__ Wloc,
+           const float* __restrict__ fnb, const int* __restrict__ conn, const float* __restrict__ fmat,
+           const unsigned char* __restrict__ blob, int64_t ntiles, int* __restrict__ status) {
+  using L = Layout<N>;
+  constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPN = L::KPN, NPL = L::NPL;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPN
+  unsigned char* opb = opa + 2 * L::OPN_SPLIT;                    // Rhat operand
+  float* stage = reinterpret_cast<float*>(opb + L::BLOB_N);       // 2 x [BT][9][32]
+  TcShared* ts = reinterpret_cast<TcShared*>(stage + 2 * L::STAGE_FLOATS);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool leader = threadIdx.x == 0;
+  const uint32_t bar_ld = smem_u32(&ts->bar[0]), bar_mma = smem_u32(&ts->bar[1]);
+  constexpr int NCOLS = (3 * NPL <= 128) ? 128 : ((3 * NPL <= 256) ? 256 : 512);
+
+  for (int i = threadIdx.x; i < 2 * L::OPN_SPLIT / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(opa)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (w == 0) tmem_alloc<NCOLS>(ts);
+  if (leader) {
+    mbar_init(bar_ld, 1);
+    mbar_init(bar_mma, 1);
+    mbar_fence_init();
+  }
+  fence_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = ts->tmem;
+  if (leader) load_operands(opb, blob, L::BLOB_N, bar_ld);
+  bool ok = __syncthreads_and(tc_wait(bar_ld, 0)) != 0;
+  uint32_t phase = 0;
+  bool pending = false;
+  uint32_t pending_phase = 0;
+  const int g = group_of(w);
+  const uint32_t my_tmem = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(g * NPL);
+  const int my_row = op_row(w, lane);
+  const uint32_t opa_s = smem_u32(opa), opb_s = smem_u32(opb);
+
+  for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    const size_t e = (size_t)tile * kTile + lane;
+    const float* Ft = fnb + tile * (4 * kNq * kNq * kTile);
+    auto prefetch = [&](auto face) {
+      constexpr int s = decltype(face)::value;
+      const int c = __ldg(conn + e * 4 + s);
+      const size_t nb = (size_t)(c >> 7);
+      const int j = (c >> 2) & 3;
+      const float* P = Pface + ((nb * 4 + j) * kNq + w) * (size_t)BT;
+      float* dst = stage + (s & 1) * L::STAGE_FLOATS + w * kTile + lane;
+#pragma unroll
+      for (int n = 0; n < BT; ++n) cp_async_elem(dst + n * kNq * kTile, P + n);
+      cp_async_commit();
+    };
+    if constexpr (WITH_NEIGH) prefetch(std::integral_constant<int, 0>{});
+    static_for<0, 4>([&](auto face) {
+      constexpr int s = decltype(face)::value;
+      float Wr[BT];
+#pragma unroll
+      for (int m = 0; m < BT; ++m)
+        Wr[m] = WITH_LOCAL ? __ldg(Wloc + ((tile * 4 + s) * kNq * BT + w * BT + m) * kTile + lane) : 0.0f;
+      if constexpr (WITH_NEIGH) {
+        float* Xsh = stage + (s & 1) * L::STAGE_FLOATS;
+        const int h = __ldg(conn + e * 4 + s) & 3;
+        if constexpr (s < 3) {
+          prefetch(std::integral_constant<int, s + 1>{});
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        float Pn[BT];
+#pragma unroll
+        for (int n = 0; n < BT; ++n) Pn[n] = Xsh[(n * kNq + w) * kTile + lane];
+        const float* fh = fmat + (size_t)h * BT * BT;
+        // V[m][q] = sum_n f^h_mn Pn[n], f^h block-diagonal by polynomial degree
+#pragma unroll
+        for (int d = 0; d <= N; ++d) {
+          const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
+#pragma unroll
+          for (int m = lo; m < hi; ++m) {
+            float v = 0.0f;
+#pragma unroll
+            for (int n = lo; n < hi; ++n) v = fmaf(__ldg(fh + m + n * BT), Pn[n], v);
+            Xsh[(m * kNq + w) * kTile + lane] = v;
+          }
+        }
+        float a[kNq];
+#pragma unroll
+        for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < BT; ++m) {
+          float v = Wr[m];
+#pragma unroll
+          for (int q = 0; q < kNq; ++q) v = fmaf(a[q], Xsh[(m * kNq + q) * kTile + lane], v);
+          Wr[m] = v;
+        }
+        __syncthreads();
+      }
+      // W^s into the element operand at K = s * BT8 + m
+      static_for<0, BT8 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (8 * c + i < BT) ? Wr[(8 * c + i < BT) ? 8 * c + i : 0] : 0.0f;
+        store_split8(opa, L::OPN_SPLIT, op_offset(my_row, s * BT8 + 8 * c, KPN), v);
+      });
+    });
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (leader && ok) {
+      fence_after_sync();
+      issue_pass(tmem, NPL, opa_s, L::OPN_SPLIT, KPN, opb_s, NPL, KPN, bar_mma);
+    }
+    const bool was_ok = ok;
+    const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
+    ok = __syncthreads_and(done) != 0;
+    if (was_ok && !ok) {
+      pending = true;
+      pending_phase = phase;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    double* Qt = Q + tile * (kNq * B * kTile);
+    static_for<0, up8(B) / 8>([&](auto cc) {
+      constexpr int k0 = decltype(cc)::value * 8;
+      float r[8];
+      tmem_ld8(my_tmem + k0, r);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (k0 + i < B) Qt[(w * B + k0 + i) * kTile + lane] += (double)r[i];
+    });
+    fence_before_sync();
+    __syncthreads();
+  }
+  if (pending) (void)tc_wait(bar_mma, pending_phase);
+  if (!ok && leader) atomicExch(status, kStatusTimeout);
+  fence_before_sync();
+  __syncthreads();
+  if (w == 0) {
+    fence_after_sync();
+    tmem_free<NCOLS>(tmem);
+  }
+}
+
+// ------------------------------------------------------------------ launch helpers
+struct TcLaunch {
+  int64_t ntiles;
+  int64_t tile0;             // first tile of the launch (per-tile pointers are offset to it)
+  unsigned grid;             // persistent CTAs
+  double *Q, *I;
+  float *Pface, *Wloc;       // Pface: all elements (k_local_tc writes at tile0 onwards)
+  const float *star, *floc, *fnb, *f;
+  const int* conn;
+  const unsigned char *blob_local, *blob_neigh;
+  double dt;
+  StarPattern SP;
+  int* status;
+  cudaStream_t stream;
+};
+
+}  // namespace tc
+
+// Entry points of the tensor-core kernels (ader_tc.cu): shared-memory sizes, host
+// construction of the split global-matrix operands, attributes and launches.
+size_t tc_smem_local(int N);
+size_t tc_smem_neigh(int N);
+bool tc_supported(int N);
+void tc_operands_local(int N, std::vector<unsigned char>& out);
+void tc_operands_neigh(int N, std::vector<unsigned char>& out);
+void tc_set_attributes(int N);
+void tc_launch_local(int N, const tc::TcLaunch& L);
+// variant 0: local + neighbour products (fused step), 1: neighbour only, 2: local only
+void tc_launch_neigh(int N, const tc::TcLaunch& L, int variant);
+
+}  // namespace yt

@@ -2,6 +2,7 @@
 // entry points yt_solver_* / yt_step* (Sec. 5.1 of the paper).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "ader_kernels.cuh"
+#include "ader_tc.cuh"
 #include "common.h"
 #include "solver_internal.h"
 #include "tables.h"
@@ -205,7 +207,7 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.groups = FaceGroups{};
   L.groups.base[0] = s->Pface;
   L.groups.bt[0] = s->BT;
-  const bool f32 = s->prec == YT_F32;
+  const bool f32 = s->prec != YT_F64;
   L.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
   L.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
   L.dt = s->dt;
@@ -237,6 +239,18 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
 // and the exchange buffer, k_neigh the four faces' flux products.
 void set_smem(yt_solver* s) {
   const int N = s->N;
+  if (s->prec == YT_BF16X3_F32ACC) {
+    s->smem_local = tc_smem_local(N);
+    s->smem_neigh = tc_smem_neigh(N);
+    int dev = 0, optin = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device attribute");
+    YT_REQUIRE(s->smem_local <= (size_t)optin && s->smem_neigh <= (size_t)optin, YT_ERR_UNSUPPORTED,
+               "tensor-core step: shared memory of this order exceeds the device limit");
+    tc_set_attributes(N);
+    cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
+    return;
+  }
   const int B = n_basis(N), BT = n_face_basis(N);
   const int KC = BT / 3 > 0 ? BT / 3 : 1;
   const int XR = 3 * KC > BT ? 3 * KC : BT;
@@ -251,13 +265,69 @@ void set_smem(yt_solver* s) {
   cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
 }
 
+tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt = -1) {
+  tc::TcLaunch L;
+  if (nt < 0) nt = s->ntiles;
+  const size_t e0 = (size_t)t0 * kTile;
+  L.ntiles = nt;
+  L.tile0 = t0;
+  L.grid = (unsigned)std::min<int64_t>(nt, s->tc_grid);
+  L.Q = s->Q + e0 * kNq * s->B;
+  L.I = s->I + e0 * kNq * s->B;
+  L.Pface = static_cast<float*>(s->Pface);             // gathered by absolute index
+  L.Wloc = static_cast<float*>(s->Wloc) + e0 * 4 * kNq * s->BT;
+  L.star = static_cast<const float*>(s->star_r) + e0 * 3 * kStarSlots;
+  L.floc = static_cast<const float*>(s->floc_r) + e0 * 4 * 81;
+  L.fnb = static_cast<const float*>(s->fnb_r) + e0 * 4 * 81;
+  L.f = s->d_f32;
+  L.conn = s->conn + e0 * 4;
+  L.blob_local = s->d_tc_local;
+  L.blob_neigh = s->d_tc_neigh;
+  L.dt = s->dt;
+  L.SP = kStar;
+  L.status = s->d_status;
+  L.stream = st;
+  return L;
+}
+
+// Launch arguments restricted to tiles [t0, t0 + nt): every per-tile array is offset;
+// the neighbour kernel still gathers face projections of all elements (groups.base).
+AderLaunch chunk_args(const AderLaunch& F, const yt_solver* s, int64_t t0, int64_t nt) {
+  AderLaunch L = F;
+  const size_t rb = s->real_bytes;
+  L.ntiles = nt;
+  L.Q += (size_t)t0 * kNq * s->B * kTile;
+  L.I += (size_t)t0 * kNq * s->B * kTile;
+  L.Pface = static_cast<unsigned char*>(L.Pface) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
+  L.Wloc = static_cast<unsigned char*>(L.Wloc) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
+  L.star = static_cast<const unsigned char*>(L.star) + (size_t)t0 * 3 * kStarSlots * kTile * rb;
+  L.floc = static_cast<const unsigned char*>(L.floc) + (size_t)t0 * 4 * 81 * kTile * rb;
+  L.fnb = static_cast<const unsigned char*>(L.fnb) + (size_t)t0 * 4 * 81 * kTile * rb;
+  L.conn += (size_t)t0 * kTile * 4;
+  return L;
+}
+
+// Tensor-core form: k_local_tc writes the local flux products, and the lifting kernel
+// adds them (fused step: with the neighbour products) through Rhat^s.
 void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
+  if (s->prec == YT_BF16X3_F32ACC) {
+    const tc::TcLaunch T = tc_args(s, st);
+    tc_launch_local(s->N, T);
+    if (!fused) tc_launch_neigh(s->N, T, 2);
+    cuda_check(cudaGetLastError(), "k_local_tc launch");
+    return;
+  }
   const AderLaunch L = launch_args(s, st);
   if (fused) YT_VARIANT_SWITCH(ader_launch, lf, L);
   else YT_VARIANT_SWITCH(ader_launch, ll, L);
   cuda_check(cudaGetLastError(), "k_local launch");
 }
 void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
+  if (s->prec == YT_BF16X3_F32ACC) {
+    tc_launch_neigh(s->N, tc_args(s, st), fused ? 0 : 1);
+    cuda_check(cudaGetLastError(), "k_neigh_tc launch");
+    return;
+  }
   const AderLaunch L = launch_args(s, st);
   if (fused) YT_VARIANT_SWITCH(ader_launch, nf, L);
   else YT_VARIANT_SWITCH(ader_launch, np, L);
@@ -319,6 +389,24 @@ void build_tables(yt_solver* s) {
   s->d_f = dalloc<double>(R.f.size());
   cuda_check(cudaMemcpy(s->d_val, csr.val.data(), csr.val.size() * sizeof(double), cudaMemcpyHostToDevice), "copy val");
   cuda_check(cudaMemcpy(s->d_f, R.f.data(), R.f.size() * sizeof(double), cudaMemcpyHostToDevice), "copy f");
+  if (s->prec == YT_BF16X3_F32ACC) {
+    std::vector<float> f32(R.f.begin(), R.f.end());
+    s->d_f32 = dalloc<float>(f32.size());
+    cuda_check(cudaMemcpy(s->d_f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy f32");
+    std::vector<unsigned char> ol, on;
+    tc_operands_local(N, ol);
+    tc_operands_neigh(N, on);
+    s->d_tc_local = dalloc<unsigned char>(ol.size());
+    s->d_tc_neigh = dalloc<unsigned char>(on.size());
+    s->d_status = dalloc<int>(1);
+    cuda_check(cudaMemcpy(s->d_tc_local, ol.data(), ol.size(), cudaMemcpyHostToDevice), "copy tc operands");
+    cuda_check(cudaMemcpy(s->d_tc_neigh, on.data(), on.size(), cudaMemcpyHostToDevice), "copy tc operands");
+    cuda_check(cudaMemset(s->d_status, 0, sizeof(int)), "memset status");
+    int dev = 0, sms = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+    s->tc_grid = (unsigned)std::min<int64_t>(s->ntiles, sms);
+  }
   if (s->prec == YT_F32) {
     std::vector<float> v32(csr.val.begin(), csr.val.end()), f32(R.f.begin(), R.f.end());
     // FP32 values of degrees <= 5 are also read from constant memory (one copy per kernel
@@ -347,6 +435,7 @@ namespace yt {
 AderLaunch solver_launch_args(yt_solver* s, cudaStream_t st) { return launch_args(s, st); }
 
 void solver_launch_variant(yt_solver* s, const AderLaunch& L, int variant) {
+  YT_REQUIRE(s->prec != YT_BF16X3_F32ACC, YT_ERR_UNSUPPORTED, "tile-table launches: YT_F64 or YT_F32");
   switch (variant) {
     case 0: YT_VARIANT_SWITCH(ader_launch, lf, L); break;
     case 1: YT_VARIANT_SWITCH(ader_launch, ll, L); break;
@@ -361,11 +450,11 @@ size_t solver_device_bytes(int order, yt_precision prec, int64_t n_elements) {
   const int N = order - 1;
   const size_t B = n_basis(N), BT = n_face_basis(N);
   const size_t Epad = (size_t)((n_elements + kTile - 1) / kTile) * kTile;
-  const size_t rb = prec == YT_F32 ? 4 : 8;
+  const size_t rb = prec == YT_F64 ? 8 : 4;
   size_t per = 8 * kNq * B * 3;                        // Q, I, staging
   per += 2 * rb * 4 * kNq * BT;                        // face projections, local products
   per += 8 * (3 * kStarSlots + 8 * 81);                // star matrices, flux solvers
-  if (prec == YT_F32) per += 4 * (3 * kStarSlots + 8 * 81);
+  if (prec != YT_F64) per += 4 * (3 * kStarSlots + 8 * 81);
   per += 4 * 4 + 8 * 12;                               // connectivity, setup inputs
   return Epad * per;
 }
@@ -380,10 +469,11 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
                "mesh needs n_elements > 0, material and jacobian");
     YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
     YT_REQUIRE(scheme->order >= 2 && scheme->order <= 7, YT_ERR_INVALID, "order must be 2..7");
-    YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32, YT_ERR_UNSUPPORTED,
-               "solver precision: YT_F64 or YT_F32");
+    YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32 ||
+                   scheme->precision == YT_BF16X3_F32ACC,
+               YT_ERR_UNSUPPORTED, "solver precision: YT_F64, YT_F32 or YT_BF16X3_F32ACC");
     YT_REQUIRE(scheme->precision == YT_F32 || scheme->order <= 6, YT_ERR_UNSUPPORTED,
-               "YT_F64 solver: orders 2..6 (order 7 needs YT_F32)");
+               "YT_F64 and YT_BF16X3_F32ACC solvers: orders 2..6 (order 7 needs YT_F32)");
     YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
     YT_REQUIRE(mesh->n_elements < (int64_t(1) << 24), YT_ERR_UNSUPPORTED, "at most 2^24 elements");
     const bool nb = mesh->neighbours != nullptr;
@@ -396,7 +486,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     s->ntiles = (s->E + kTile - 1) / kTile;
     s->Epad = s->ntiles * kTile;
     s->prec = scheme->precision;
-    s->real_bytes = s->prec == YT_F32 ? sizeof(float) : sizeof(double);
+    s->real_bytes = s->prec == YT_F64 ? sizeof(double) : sizeof(float);
     s->dt = scheme->dt;
     s->has_neighbours = nb;
     std::vector<int> conn;
@@ -441,7 +531,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
       e1 = cudaGetLastError();
     }
     if (e1 == cudaSuccess) {
-      if (s->prec == YT_F32) {
+      if (s->prec != YT_F64) {
         const int64_t ns = s->Epad * 3 * kStarSlots, nf = s->Epad * 4 * 81;
         s->star_r = dalloc<float>((size_t)ns);
         s->floc_r = dalloc<float>((size_t)nf);
@@ -541,6 +631,79 @@ extern "C" yt_status yt_step(yt_solver* s, yt_stream stream) {
   });
 }
 
+namespace {
+// Kernels of one phase over tiles [t0, t0 + nt) (phase 0: k_local of the fused step,
+// phase 1: k_neigh of the fused step).
+void dispatch_chunk(yt_solver* s, cudaStream_t st, int phase, int64_t t0, int64_t nt) {
+  if (s->prec == YT_BF16X3_F32ACC) {
+    const tc::TcLaunch T = tc_args(s, st, t0, nt);
+    if (phase == 0) tc_launch_local(s->N, T);
+    else tc_launch_neigh(s->N, T, 0);
+  } else {
+    const AderLaunch L = chunk_args(launch_args(s, st), s, t0, nt);
+    if (phase == 0) YT_VARIANT_SWITCH(ader_launch, lf, L);
+    else YT_VARIANT_SWITCH(ader_launch, nf, L);
+  }
+  cuda_check(cudaGetLastError(), "chunk launch");
+}
+}  // namespace
+
+extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* dofs_out,
+                                  yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s && dofs_in && dofs_out, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int kChunks = 8;
+    if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+    if (!s->copy_stream) {
+      cuda_check(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "copy stream");
+      cuda_check(cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming), "event");
+      cuda_check(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming), "event");
+      for (int c = 0; c < kChunks; ++c) {
+        cuda_check(cudaEventCreateWithFlags(&s->ev_in[c], cudaEventDisableTiming), "event");
+        cuda_check(cudaEventCreateWithFlags(&s->ev_out[c], cudaEventDisableTiming), "event");
+      }
+    }
+    cudaStream_t cp = s->copy_stream;
+    const int64_t per = (s->ntiles + kChunks - 1) / kChunks;     // tiles per chunk
+    const size_t row = (size_t)kNq * s->B;                       // doubles per element
+    cuda_check(cudaEventRecord(s->ev_start, st), "event record");
+    cuda_check(cudaStreamWaitEvent(cp, s->ev_start, 0), "stream wait");
+    // uploads on the copy stream; layout conversion and local kernel per chunk on `st`
+    for (int c = 0; c < kChunks; ++c) {
+      const int64_t t0 = c * per, nt = std::min<int64_t>(per, s->ntiles - t0);
+      if (nt <= 0) break;
+      const int64_t e0 = t0 * kTile, ne = std::min<int64_t>(nt * kTile, s->E - e0);
+      cuda_check(cudaMemcpyAsync(s->staging + e0 * row, dofs_in + e0 * row, (size_t)ne * row * sizeof(double),
+                                 cudaMemcpyHostToDevice, cp), "H2D chunk");
+      cuda_check(cudaEventRecord(s->ev_in[c], cp), "event record");
+      cuda_check(cudaStreamWaitEvent(st, s->ev_in[c], 0), "stream wait");
+      const int64_t total = nt * kTile * (int64_t)row;
+      k_to_blocked<<<blocks_for(total, 256), 256, 0, st>>>(s->staging + e0 * row, s->Q + e0 * row, ne,
+                                                           nt * kTile, s->B);
+      cuda_check(cudaGetLastError(), "k_to_blocked");
+      dispatch_chunk(s, st, 0, t0, nt);
+    }
+    // neighbour kernel per chunk (after every local chunk), layout back, downloads
+    for (int c = 0; c < kChunks; ++c) {
+      const int64_t t0 = c * per, nt = std::min<int64_t>(per, s->ntiles - t0);
+      if (nt <= 0) break;
+      const int64_t e0 = t0 * kTile, ne = std::min<int64_t>(nt * kTile, s->E - e0);
+      dispatch_chunk(s, st, 1, t0, nt);
+      k_from_blocked<<<blocks_for(ne * (int64_t)row, 256), 256, 0, st>>>(s->Q + e0 * row,
+                                                                         s->staging + e0 * row, ne, s->B);
+      cuda_check(cudaGetLastError(), "k_from_blocked");
+      cuda_check(cudaEventRecord(s->ev_out[c], st), "event record");
+      cuda_check(cudaStreamWaitEvent(cp, s->ev_out[c], 0), "stream wait");
+      cuda_check(cudaMemcpyAsync(dofs_out + e0 * row, s->staging + e0 * row, (size_t)ne * row * sizeof(double),
+                                 cudaMemcpyDeviceToHost, cp), "D2H chunk");
+    }
+    cuda_check(cudaEventRecord(s->ev_done, cp), "event record");
+    cuda_check(cudaStreamWaitEvent(st, s->ev_done, 0), "stream wait");
+  });
+}
+
 extern "C" yt_status yt_solver_stats(const yt_solver* s, double* lf, double* nf, double* lb,
                                      double* nbb) {
   return guarded([&] {
@@ -549,6 +712,21 @@ extern "C" yt_status yt_solver_stats(const yt_solver* s, double* lf, double* nf,
     if (nf) *nf = s->flops_neigh;
     if (lb) *lb = s->bytes_local;
     if (nbb) *nbb = s->bytes_neigh;
+  });
+}
+
+extern "C" yt_status yt_solver_status(yt_solver* s, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cuda_check(cudaStreamSynchronize(st), "stream synchronize");
+    if (!s->d_status) return;
+    int v = 0;
+    cuda_check(cudaMemcpy(&v, s->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status copy");
+    if (v != 0) {
+      cuda_check(cudaMemset(s->d_status, 0, sizeof(int)), "status reset");
+      throw Error(YT_ERR_TIMEOUT, "a bounded device-side wait of the tensor-core kernels ran out");
+    }
   });
 }
 

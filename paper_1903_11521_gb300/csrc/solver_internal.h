@@ -15,7 +15,8 @@ struct yt_solver {
   bool has_neighbours = false;
   double *Q = nullptr, *I = nullptr, *star = nullptr, *floc = nullptr, *fnb = nullptr,
          *staging = nullptr;
-  // buffers of the contraction type (double for YT_F64, float for YT_F32)
+  // buffers of the contraction type (double for YT_F64, float for YT_F32 and the
+  // tensor-core form YT_BF16X3_F32ACC, whose per-element products run in binary32)
   void *Pface = nullptr, *Wloc = nullptr, *star_r = nullptr, *floc_r = nullptr, *fnb_r = nullptr;
   int* conn = nullptr;
   double* d_val = nullptr;
@@ -27,11 +28,26 @@ struct yt_solver {
   double flops_local_unfused = 0;
   int64_t n_values = 0;
   size_t smem_local = 0, smem_neigh = 0;
+  // tensor-core form: split-bf16 global-matrix operands of the two kernels, persistent
+  // grid size and the status word of the bounded device-side waits
+  unsigned char *d_tc_local = nullptr, *d_tc_neigh = nullptr;
+  int* d_status = nullptr;
+  unsigned tc_grid = 0;
+  // yt_step_host: copy stream and per-chunk events (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_in[16] = {}, ev_out[16] = {};
   ~yt_solver() {
     if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
+    for (cudaEvent_t e : ev_in) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_out) if (e) cudaEventDestroy(e);
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_done) cudaEventDestroy(ev_done);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
                     floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
-                    (void*)d_val32, (void*)d_f32})
+                    (void*)d_val32, (void*)d_f32, (void*)d_tc_local, (void*)d_tc_neigh,
+                    (void*)d_status})
       if (p) cudaFree(p);
   }
 };

@@ -104,8 +104,18 @@ class Solver:
         _lib.check(self.lib.yt_step_neighbour(self.handle, _stream_handle(stream)),
                    "yt_step_neighbour")
 
+    def step_host_ptr(self, in_ptr: int, out_ptr: int, stream=None):
+        """One step on host buffers (canonical layout), copies pipelined with the kernels."""
+        _lib.check(self.lib.yt_step_host(self.handle, in_ptr, out_ptr, _stream_handle(stream)),
+                   "yt_step_host")
+
     def step_phase(self, phase: int, stream=None):
         _lib.check(self.lib.yt_step_phase(self.handle, phase, _stream_handle(stream)), "yt_step_phase")
+
+    def status(self, stream=None):
+        """Synchronises the stream; raises YtError (YT_ERR_TIMEOUT) if a bounded
+        device-side wait of the tensor-core kernels ran out."""
+        _lib.check(self.lib.yt_solver_status(self.handle, _stream_handle(stream)), "yt_solver_status")
 
     def stats(self):
         v = [C.c_double() for _ in range(4)]

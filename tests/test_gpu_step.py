@@ -148,6 +148,33 @@ def test_phases_equal_step_and_unfused_path(yt):
     assert rel_per_quantity(outs[2], outs[0]).max() < TOL
 
 
+@pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32", "YT_BF16X3_F32ACC"])
+def test_step_host_equals_step(yt, prec_name):
+    """yt_step_host (pipelined copies, 8 element chunks, ragged last chunk) gives bitwise
+    the result of set_dofs + yt_step + get on the same solver; also in place."""
+    import torch
+    prec = getattr(yt, prec_name)
+    E, order = 8 * 32 * 3 + 45, 4
+    el, conn, Q, dt = make_case(E, order, "impedance", seed=61)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    canon = np.ascontiguousarray(Q.transpose(0, 2, 1))
+    s = yt.Solver(order, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient, precision=prec)
+    s.set_dofs_host(Q)
+    s.step()
+    ref = s.get_host()
+    pin_in = torch.from_numpy(canon.copy()).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    s.step_host_ptr(pin_in.data_ptr(), pin_out.data_ptr())
+    torch.cuda.synchronize()
+    got = pin_out.numpy().transpose(0, 2, 1)
+    assert np.array_equal(got, ref)
+    s.step_host_ptr(pin_in.data_ptr(), pin_in.data_ptr())      # in place
+    torch.cuda.synchronize()
+    assert np.array_equal(pin_in.numpy().transpose(0, 2, 1), ref)
+    s.status()
+    s.close()
+
+
 # ------------------------------------------------------------------ precision form (FP32)
 F32_TOL_INCREMENT = 2e-5     # relative Frobenius norm per quantity of Q_new - Q
 F32_TOL_I = 2e-6             # of the time integral
