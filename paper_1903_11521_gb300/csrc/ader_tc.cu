@@ -110,9 +110,9 @@ tc::TcStep step_of(const tc::TcLaunch& L) {
 
 template <int N>
 void launch_local(const tc::TcLaunch& L) {
-  float* P = L.Pface + (size_t)L.tile0 * kTile * 4 * kNq * tc::Layout<N>::BT;
+  float* P = L.Pface + (size_t)L.tile0 * kTile * 4 * kNq * tc::Layout<N>::BT8;
   tc::k_local_tc<N><<<L.grid, tc::kRows, tc::Layout<N>::SMEM, L.stream>>>(
-      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, step_of(L), L.SP, L.ntiles, L.status);
+      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, step_of(L), L.SP, L.ntiles, L.status);
 }
 
 template <int N>
@@ -153,6 +153,13 @@ size_t tc_smem_local(int N) {
 size_t tc_smem_neigh(int N) {
   size_t r = 0;
 #define YT_C(n) r = tc::Layout<n>::SMEM_N
+  YT_TC_SWITCH(N, YT_C);
+#undef YT_C
+  return r;
+}
+size_t tc_scratch_floats(int N, unsigned grid) {
+  size_t r = 0;
+#define YT_C(n) r = (size_t)grid * tc::Layout<n>::SROWS * tc::kRows
   YT_TC_SWITCH(N, YT_C);
 #undef YT_C
   return r;

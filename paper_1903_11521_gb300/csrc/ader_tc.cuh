@@ -98,6 +98,10 @@ __host__ __device__ constexpr int tc_cs() {
   return c;
 }
 
+// first scratch row of D~^d (d >= 1): rows C(N-d+3,3) of every earlier derivative
+template <int N>
+__host__ __device__ constexpr int tc_srow(int d) { return d <= 1 ? 0 : tc_srow<N>(d - 1) + Dims<N>::nd(d - 1); }
+
 template <int N>
 struct Layout {
   using D = Dims<N>;
@@ -113,6 +117,8 @@ struct Layout {
   __host__ __device__ static constexpr int off(int p) { return tc_off<N>(p); }
   static constexpr int BLOB = tc_off<N>(NPASS);
   static constexpr int CS = tc_cs<N>();               // TMEM columns per group
+  // rows of the scaled derivatives D~^1..D~^N kept for the time integral (per-CTA scratch)
+  static constexpr int SROWS = tc_srow<N>(N + 1);
   static constexpr int OPA_SPLIT = kRows * KPA * 2;    // bytes of one split
   static constexpr int XS_FLOATS = 3 * kNq * 2 * kTile * 4;
   static constexpr size_t SMEM = (size_t)2 * OPA_SPLIT + BLOB + XS_FLOATS * 4 + 64;
@@ -121,8 +127,8 @@ struct Layout {
   static constexpr int NPL = up16(B);
   static constexpr int OPN_SPLIT = kRows * KPN * 2;
   static constexpr int BLOB_N = 2 * NPL * KPN * 2;
-  static constexpr int STAGE_FLOATS = BT * kNq * kTile;      // one face of gathered projections
-  static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 2 * STAGE_FLOATS * 4 + 64;
+  static constexpr int STAGE_FLOATS = BT8 * kNq * kTile;     // one face of gathered projections
+  static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 3 * STAGE_FLOATS * 4 + 64;
   static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
   static_assert(BT8 / 8 <= 3, "face basis too large for the exchange buffer");
 };
@@ -302,17 +308,28 @@ __device__ __forceinline__ void load_operands(unsigned char* dst, const unsigned
   }
 }
 
+// 16-byte global -> shared copy bypassing the registers (L2 only), grouped per face.
+__device__ __forceinline__ void cp_async16(float* dst_shared, const float* src_global) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst_shared)), "l"(src_global)
+               : "memory");
+}
+
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume, face projections and local flux products of tiles
 // of 32 elements; persistent CTAs (grid <= number of tiles) stride over the tiles.
-// Outputs and layouts as k_local<N, false, float>: Q (volume added), I, Pface
-// [element][4][9][BT], Wloc [tile][4][9][BT][32] = (R^sT I) Aloc_s^T.
+// Outputs and layouts as k_local<N, false, float>: Q (volume added), I, Wloc
+// [tile][4][9][BT][32] = (R^sT I) Aloc_s^T, except that the face projections Pface are
+// [element][4][9][BT8] (rows padded to 8 floats: 16-byte copies in k_neigh_tc).
+// The scaled derivatives D~^d (binary32, as produced) go to this CTA's scratch rows
+// [SROWS][9][32] (L2-resident, reused tile after tile); the time integral is summed from
+// them in binary64, in the order d = 0..N, once the derivatives are done.  Keeping the
+// binary64 accumulator in registers instead spills (168-register cap of 9-warp CTAs).
 template <int N>
 __global__ void __launch_bounds__(kRows, 1)
 k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, float* __restrict__ Wloc,
            const float* __restrict__ star, const float* __restrict__ floc,
-           const unsigned char* __restrict__ blob, TcStep T, StarPattern SP, int64_t ntiles,
-           int* __restrict__ status) {
+           const unsigned char* __restrict__ blob, float* __restrict__ scratch, TcStep T, StarPattern SP,
+           int64_t ntiles, int* __restrict__ status) {
   using L = Layout<N>;
   using Dm = Dims<N>;
   constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPA = L::KPA, NI = L::NI, CS = L::CS, NV = L::NV;
@@ -349,6 +366,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   const int g = group_of(w);
   const uint32_t my_tmem = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(g * CS);
   const int my_row = op_row(w, lane);
+  float* my_scr = scratch + (size_t)blockIdx.x * L::SROWS * kRows + w * kTile + lane;
   const int s0 = SP.start[w], cnt = SP.start[w + 1] - s0;
   int scol[3];
 #pragma unroll
@@ -423,17 +441,14 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       for (int s = 0; s < 3; ++s)
         sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : 0.0f;
 
-    // D~^0 = Q as operand; I starts as dt Q
-    double Icol[NI];
+    // D~^0 = Q as operand
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
       float v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int k = k0 + i;
-        const double q = k < B ? __ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0;
-        if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
-        v[i] = (float)q;
+        v[i] = k < B ? (float)__ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0f;
       }
       store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
     });
@@ -456,7 +471,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
           const int k = k0 + i;
           if (k < R) {
             v[i] *= (float)dt;
-            Icol[k < NI ? k : 0] = fma(dt * T.invfact[DELTA + 1], (double)v[i], Icol[k < NI ? k : 0]);
+            my_scr[(tc_srow<N>(DELTA + 1) + k) * kRows] = v[i];
           } else {
             v[i] = 0.0f;
           }
@@ -467,7 +482,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       if constexpr (DELTA + 1 < N) issue(DELTA + 1);
     });
 
-    // time integral: HBM (double) and operand
+    // time integral I = sum_d (dt / (d+1)!) D~^d in binary64: HBM and operand
     double* It = Iout + tile * (kNq * B * kTile);
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
@@ -476,7 +491,10 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       for (int i = 0; i < 8; ++i) {
         const int k = k0 + i;
         if (k < B) {
-          const double ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+          double ik = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+#pragma unroll
+          for (int d = 1; d <= N; ++d)
+            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], (double)my_scr[(tc_srow<N>(d) + k) * kRows], ik);
           It[(w * B + k) * kTile + lane] = ik;
           v[i] = (float)ik;
         } else {
@@ -513,7 +531,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 
     // face projections P^s = R^sT I -> Pface; local flux products W = P^s Aloc_s^T -> Wloc
     wait_pass();
-    float* Pe = Pface + (tile * kTile + lane) * (4 * kNq * BT);
+    float* Pe = Pface + (tile * kTile + lane) * (4 * kNq * BT8);
     const float* Ft = floc + tile * (4 * kNq * kNq * kTile);
     float* Wt = Wloc + tile * (4 * kNq * BT * kTile);
     static_for<0, 4>([&](auto face) {
@@ -522,9 +540,9 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         constexpr int c = decltype(cc)::value;
         float r[8];
         tmem_ld8(my_tmem + s * BT8 + 8 * c, r);
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (8 * c + i < BT) Pe[(s * kNq + w) * BT + 8 * c + i] = r[i];
+        float4* pe = reinterpret_cast<float4*>(Pe + (s * kNq + w) * BT8 + 8 * c);
+        pe[0] = make_float4(r[0], r[1], r[2], r[3]);
+        pe[1] = make_float4(r[4], r[5], r[6], r[7]);
         float4* dst = reinterpret_cast<float4*>(xs) + ((c * kNq + w) * 2) * kTile + lane;
         dst[0] = make_float4(r[0], r[1], r[2], r[3]);
         dst[kTile] = make_float4(r[4], r[5], r[6], r[7]);
@@ -586,8 +604,9 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPN
   unsigned char* opb = opa + 2 * L::OPN_SPLIT;                    // Rhat operand
-  float* stage = reinterpret_cast<float*>(opb + L::BLOB_N);       // 2 x [BT][9][32]
-  TcShared* ts = reinterpret_cast<TcShared*>(stage + 2 * L::STAGE_FLOATS);
+  float* stage = reinterpret_cast<float*>(opb + L::BLOB_N);       // 2 x [9][32][BT8] gathered
+  float* xs = stage + 2 * L::STAGE_FLOATS;                        // [BT8/4][9][32][4]
+  TcShared* ts = reinterpret_cast<TcShared*>(xs + L::STAGE_FLOATS);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool leader = threadIdx.x == 0;
   const uint32_t bar_ld = smem_u32(&ts->bar[0]), bar_mma = smem_u32(&ts->bar[1]);
@@ -619,15 +638,17 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
   for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
     const size_t e = (size_t)tile * kTile + lane;
     const float* Ft = fnb + tile * (4 * kNq * kNq * kTile);
+    // the neighbour's projection row (its face j, quantity w) into this thread's column
+    // of the face's staging slot; issued one face ahead
     auto prefetch = [&](auto face) {
       constexpr int s = decltype(face)::value;
       const int c = __ldg(conn + e * 4 + s);
       const size_t nb = (size_t)(c >> 7);
       const int j = (c >> 2) & 3;
-      const float* P = Pface + ((nb * 4 + j) * kNq + w) * (size_t)BT;
-      float* dst = stage + (s & 1) * L::STAGE_FLOATS + w * kTile + lane;
+      const float* P = Pface + ((nb * 4 + j) * kNq + w) * (size_t)BT8;
+      float* dst = stage + (s & 1) * L::STAGE_FLOATS + (w * kTile + lane) * BT8;
 #pragma unroll
-      for (int n = 0; n < BT; ++n) cp_async_elem(dst + n * kNq * kTile, P + n);
+      for (int n = 0; n < BT8; n += 4) cp_async16(dst + n, P + n);
       cp_async_commit();
     };
     if constexpr (WITH_NEIGH) prefetch(std::integral_constant<int, 0>{});
@@ -638,7 +659,6 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
       for (int m = 0; m < BT; ++m)
         Wr[m] = WITH_LOCAL ? __ldg(Wloc + ((tile * 4 + s) * kNq * BT + w * BT + m) * kTile + lane) : 0.0f;
       if constexpr (WITH_NEIGH) {
-        float* Xsh = stage + (s & 1) * L::STAGE_FLOATS;
         const int h = __ldg(conn + e * 4 + s) & 3;
         if constexpr (s < 3) {
           prefetch(std::integral_constant<int, s + 1>{});
@@ -646,11 +666,22 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
         } else {
           cp_async_wait<0>();
         }
-        float Pn[BT];
+        float Pn[BT8];
+        const float4* own = reinterpret_cast<const float4*>(stage + (s & 1) * L::STAGE_FLOATS +
+                                                            (w * kTile + lane) * BT8);
 #pragma unroll
-        for (int n = 0; n < BT; ++n) Pn[n] = Xsh[(n * kNq + w) * kTile + lane];
+        for (int n4 = 0; n4 < BT8 / 4; ++n4) {
+          const float4 t = own[n4];
+          Pn[4 * n4] = t.x;
+          Pn[4 * n4 + 1] = t.y;
+          Pn[4 * n4 + 2] = t.z;
+          Pn[4 * n4 + 3] = t.w;
+        }
         const float* fh = fmat + (size_t)h * BT * BT;
         // V[m][q] = sum_n f^h_mn Pn[n], f^h block-diagonal by polynomial degree
+        float V[BT8];
+#pragma unroll
+        for (int m = BT; m < BT8; ++m) V[m] = 0.0f;
 #pragma unroll
         for (int d = 0; d <= N; ++d) {
           const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
@@ -659,19 +690,27 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
             float v = 0.0f;
 #pragma unroll
             for (int n = lo; n < hi; ++n) v = fmaf(__ldg(fh + m + n * BT), Pn[n], v);
-            Xsh[(m * kNq + w) * kTile + lane] = v;
+            V[m] = v;
           }
         }
+        float4* xw = reinterpret_cast<float4*>(xs) + w * kTile + lane;
+#pragma unroll
+        for (int m4 = 0; m4 < BT8 / 4; ++m4)
+          xw[m4 * kNq * kTile] = make_float4(V[4 * m4], V[4 * m4 + 1], V[4 * m4 + 2], V[4 * m4 + 3]);
         float a[kNq];
 #pragma unroll
         for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < BT; ++m) {
-          float v = Wr[m];
+        for (int m4 = 0; m4 < BT8 / 4; ++m4) {
 #pragma unroll
-          for (int q = 0; q < kNq; ++q) v = fmaf(a[q], Xsh[(m * kNq + q) * kTile + lane], v);
-          Wr[m] = v;
+          for (int q = 0; q < kNq; ++q) {
+            const float4 x = reinterpret_cast<const float4*>(xs)[(m4 * kNq + q) * kTile + lane];
+            if (4 * m4 < BT) Wr[4 * m4 < BT ? 4 * m4 : 0] = fmaf(a[q], x.x, Wr[4 * m4 < BT ? 4 * m4 : 0]);
+            if (4 * m4 + 1 < BT) Wr[4 * m4 + 1 < BT ? 4 * m4 + 1 : 0] = fmaf(a[q], x.y, Wr[4 * m4 + 1 < BT ? 4 * m4 + 1 : 0]);
+            if (4 * m4 + 2 < BT) Wr[4 * m4 + 2 < BT ? 4 * m4 + 2 : 0] = fmaf(a[q], x.z, Wr[4 * m4 + 2 < BT ? 4 * m4 + 2 : 0]);
+            if (4 * m4 + 3 < BT) Wr[4 * m4 + 3 < BT ? 4 * m4 + 3 : 0] = fmaf(a[q], x.w, Wr[4 * m4 + 3 < BT ? 4 * m4 + 3 : 0]);
+          }
         }
         __syncthreads();
       }
@@ -732,6 +771,7 @@ struct TcLaunch {
   const float *star, *floc, *fnb, *f;
   const int* conn;
   const unsigned char *blob_local, *blob_neigh;
+  float* scratch;            // grid x Layout<N>::SROWS x 288 floats
   double dt;
   StarPattern SP;
   int* status;
@@ -744,6 +784,7 @@ struct TcLaunch {
 // construction of the split global-matrix operands, attributes and launches.
 size_t tc_smem_local(int N);
 size_t tc_smem_neigh(int N);
+size_t tc_scratch_floats(int N, unsigned grid);
 bool tc_supported(int N);
 void tc_operands_local(int N, std::vector<unsigned char>& out);
 void tc_operands_neigh(int N, std::vector<unsigned char>& out);

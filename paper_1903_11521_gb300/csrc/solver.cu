@@ -282,6 +282,7 @@ tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt =
   L.f = s->d_f32;
   L.conn = s->conn + e0 * 4;
   L.blob_local = s->d_tc_local;
+  L.scratch = s->d_tc_scratch;
   L.blob_neigh = s->d_tc_neigh;
   L.dt = s->dt;
   L.SP = kStar;
@@ -406,6 +407,7 @@ void build_tables(yt_solver* s) {
     cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
     s->tc_grid = (unsigned)std::min<int64_t>(s->ntiles, sms);
+    s->d_tc_scratch = dalloc<float>(tc_scratch_floats(N, s->tc_grid));
   }
   if (s->prec == YT_F32) {
     std::vector<float> v32(csr.val.begin(), csr.val.end()), f32(R.f.begin(), R.f.end());
@@ -509,7 +511,10 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     const size_t nq = (size_t)s->Epad * kNq * s->B;
     s->Q = dalloc<double>(nq);
     s->I = dalloc<double>(nq);
-    s->Pface = dalloc<unsigned char>((size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes);
+    // face projections: rows of BT values, padded to 8 in the tensor-core form
+    const size_t pbytes = (size_t)s->Epad * 4 * kNq *
+                          (s->prec == YT_BF16X3_F32ACC ? (size_t)tc::up8(s->BT) : (size_t)s->BT) * s->real_bytes;
+    s->Pface = dalloc<unsigned char>(pbytes);
     s->Wloc = dalloc<unsigned char>((size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes);
     s->star = dalloc<double>((size_t)s->Epad * 3 * kStarSlots);
     s->floc = dalloc<double>((size_t)s->Epad * 4 * 81);
@@ -517,7 +522,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     s->conn = dalloc<int>((size_t)s->Epad * 4);
     cuda_check(cudaMemsetAsync(s->Q, 0, nq * sizeof(double), st), "memset Q");
     cuda_check(cudaMemsetAsync(s->I, 0, nq * sizeof(double), st), "memset I");
-    cuda_check(cudaMemsetAsync(s->Pface, 0, (size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes, st), "memset P");
+    cuda_check(cudaMemsetAsync(s->Pface, 0, pbytes, st), "memset P");
     cuda_check(cudaMemsetAsync(s->conn, 0, (size_t)s->Epad * 4 * sizeof(int), st), "memset conn");
     if (nb) cuda_check(cudaMemcpyAsync(s->conn, conn.data(), conn.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy conn");
     double* dmat = dalloc<double>((size_t)s->E * 3);

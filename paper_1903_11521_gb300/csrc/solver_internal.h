@@ -31,6 +31,7 @@ struct yt_solver {
   // tensor-core form: split-bf16 global-matrix operands of the two kernels, persistent
   // grid size and the status word of the bounded device-side waits
   unsigned char *d_tc_local = nullptr, *d_tc_neigh = nullptr;
+  float* d_tc_scratch = nullptr;
   int* d_status = nullptr;
   unsigned tc_grid = 0;
   // yt_step_host: copy stream and per-chunk events (created on first use)
@@ -46,7 +47,7 @@ struct yt_solver {
     if (copy_stream) cudaStreamDestroy(copy_stream);
     for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
                     floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
-                    (void*)d_val32, (void*)d_f32, (void*)d_tc_local, (void*)d_tc_neigh,
+                    (void*)d_val32, (void*)d_f32, (void*)d_tc_local, (void*)d_tc_neigh, (void*)d_tc_scratch,
                     (void*)d_status})
       if (p) cudaFree(p);
   }
