@@ -308,6 +308,14 @@ yt_status yt_server_stats_get(struct yt_server* server, yt_server_stats* out);
 /* Finishes every submitted request, then stops the worker and frees the server. */
 void yt_server_destroy(struct yt_server* server);
 
+/* Host-only diagnostics: the global-matrix operands of the tensor-core kernels of an order
+ * (2..6) as uploaded by a YT_BF16X3_F32ACC solver; kernel 0 = the local kernel (passes:
+ * CK derivatives, volume chunks, face projections), 1 = the neighbour kernel (lifting).
+ * Each pass is an N x K matrix stored twice (bf16 hi parts, then lo parts) in the
+ * K-major canonical layout of 8 x 8 core matrices: entry (n, k) at byte
+ * (n/8)*16K + (k/8)*128 + (n%8)*16 + (k%8)*2.  `bytes` receives the size; pass out == NULL
+ * to query it.  No counterpart in the paper. */
+yt_status yt_tc_operands(int32_t order, int32_t kernel, unsigned char* out, int64_t* bytes);
 /* Host-only: reference matrices for an order without creating a solver (same meaning as
  * yt_solver_reference_matrix).  Runs no device code. */
 yt_status yt_reference_matrix(int32_t order, const char* name, double* out, int64_t* count);

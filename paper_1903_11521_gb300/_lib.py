@@ -90,6 +90,7 @@ SIGNATURES = {
     "yt_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "yt_server_destroy": (None, [_P]),
     "yt_reference_matrix": (C.c_int, [C.c_int32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "yt_tc_operands": (C.c_int, [C.c_int32, C.c_int32, _P, C.POINTER(C.c_int64)]),
 }
 
 

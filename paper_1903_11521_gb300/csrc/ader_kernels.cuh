@@ -175,6 +175,15 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
   }
 }
 
+// Resident CTAs per SM requested from the compiler (__launch_bounds__): the FP64 kernels
+// run one 9-warp CTA per SM (168 registers); the FP32 neighbour kernels and the FP32
+// local kernels of degree <= 4 fit 96 registers without spilling and run two CTAs per SM
+// (18 warps) to hide shared-memory and dependency latency.
+template <int N, typename Real, bool LOCAL>
+struct MinBlocks {
+  static constexpr int value = (sizeof(Real) == 4 && (!LOCAL || N <= 4)) ? 2 : 1;
+};
+
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume and local flux of one tile of 32 elements.
 //   Q, Qout : [tile][9][B][32] double   (may alias)
@@ -189,7 +198,7 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
 //                                       neighbour contribution in k_neigh)
 // LIFT = true applies the local flux here (Q is then the complete local update).
 template <int N, bool LIFT, typename Real>
-__global__ void __launch_bounds__(kNq * kTile, 1)
+__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value))
 k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
         const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
@@ -350,7 +359,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The four faces' W (BT x 9 each) stay in shared memory; every row k of Q is then
 // updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
 template <int N, bool WITH_LOCAL, typename Real>
-__global__ void __launch_bounds__(kNq * kTile, 1)
+__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, false>::value))
 k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
         StepTables<Real> T, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;

@@ -191,3 +191,17 @@ void tc_launch_neigh(int N, const tc::TcLaunch& L, int variant) {
 }
 
 }  // namespace yt
+
+// Host-only: the split global-matrix operands of the tensor-core kernels (diagnostics).
+extern "C" yt_status yt_tc_operands(int32_t order, int32_t kernel, unsigned char* out, int64_t* bytes) {
+  return yt::guarded([&] {
+    YT_REQUIRE(bytes, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(order >= 2 && order <= 6, YT_ERR_UNSUPPORTED, "tensor-core operands: orders 2..6");
+    YT_REQUIRE(kernel == 0 || kernel == 1, YT_ERR_INVALID, "kernel must be 0 (local) or 1 (neighbour)");
+    std::vector<unsigned char> v;
+    if (kernel == 0) yt::tc_operands_local(order - 1, v);
+    else yt::tc_operands_neigh(order - 1, v);
+    *bytes = (int64_t)v.size();
+    if (out) std::memcpy(out, v.data(), v.size());
+  });
+}

@@ -24,9 +24,9 @@
 // matrices of 128 contiguous bytes (a row's 8 K-consecutive values in 16 bytes),
 // K-adjacent core matrices 128 bytes apart, groups of 8 rows kp * 16 bytes apart.
 //
-// Synchronisation.  One elected thread issues the MMAs of a pass and commits them to an
-// mbarrier; all threads wait for it (bounded, see tc_wait) before reading the
-// accumulators with tcgen05.ld.  Every device-side wait gives up after kTcWaitNs and
+// Synchronisation.  One elected thread per accumulator group issues that group's MMAs of
+// a pass and commits them to an mbarrier; all threads wait for it (bounded, see tc_wait)
+// before reading the accumulators with tcgen05.ld.  Every device-side wait gives up after kTcWaitNs and
 // reports YT_ERR_TIMEOUT through the status word; the kernel then issues no further MMA,
 // finishes its tile, waits (bounded) for what it issued and frees its tensor memory.
 #pragma once
@@ -252,22 +252,24 @@ __device__ __forceinline__ void store_split8(unsigned char* op, int split_bytes,
   *reinterpret_cast<uint4*>(op + split_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// The MMAs of one pass (elected thread): three groups x K steps of 16 x three products.
-__device__ __forceinline__ void issue_pass(uint32_t tmem, int cs, uint32_t a_base, int a_split, int kpa,
-                                           uint32_t b_base, int np, int kp, uint32_t bar) {
+// The MMAs of one pass for accumulator group g (K steps of 16 x three products), issued
+// by one elected thread per group (lane 0 of warps 0..2: the three groups' MMAs are
+// independent and issue in parallel) and committed to `bar` (expected count 3).  The
+// descriptors of step j differ from step 0 only in the start address (+256 B, i.e. +16
+// in the address field, which cannot carry: shared addresses are below 256 KB).
+__device__ __forceinline__ void issue_group(int g, uint32_t tmem, int cs, uint32_t a_base, int a_split,
+                                            int kpa, uint32_t b_base, int np, int kp, uint32_t bar) {
   const uint32_t idesc = idesc_bf16(np);
   const uint32_t sbo_a = (uint32_t)kpa * 16, sbo_b = (uint32_t)kp * 16;
-  const uint32_t b_lo = b_base + (uint32_t)(np * kp * 2);
-  for (int g = 0; g < 3; ++g) {
-    const uint32_t a_hi = a_base + (uint32_t)(group_first_row(g) / 8) * sbo_a;
-    const uint32_t a_lo = a_hi + (uint32_t)a_split;
-    const uint32_t d = tmem + (uint32_t)(g * cs);
-    for (int j = 0; j < kp / 16; ++j) {
-      const uint32_t dk = (uint32_t)j * 256;
-      mma_bf16(d, smem_desc(a_hi + dk, sbo_a), smem_desc(b_base + dk, sbo_b), idesc, j > 0);
-      mma_bf16(d, smem_desc(a_hi + dk, sbo_a), smem_desc(b_lo + dk, sbo_b), idesc, 1);
-      mma_bf16(d, smem_desc(a_lo + dk, sbo_a), smem_desc(b_base + dk, sbo_b), idesc, 1);
-    }
+  const uint32_t a_hi = a_base + (uint32_t)(group_first_row(g) / 8) * sbo_a;
+  const uint64_t dah = smem_desc(a_hi, sbo_a), dal = smem_desc(a_hi + (uint32_t)a_split, sbo_a);
+  const uint64_t dbh = smem_desc(b_base, sbo_b), dbl = smem_desc(b_base + (uint32_t)(np * kp * 2), sbo_b);
+  const uint32_t d = tmem + (uint32_t)(g * cs);
+  for (int j = 0; j < kp / 16; ++j) {
+    const uint64_t dk = (uint64_t)(j * 16);
+    mma_bf16(d, dah + dk, dbh + dk, idesc, j > 0);
+    mma_bf16(d, dah + dk, dbl + dk, idesc, 1);
+    mma_bf16(d, dal + dk, dbh + dk, idesc, 1);
   }
   mma_commit(bar);
 }
@@ -348,7 +350,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   if (w == 0) tmem_alloc<512>(ts);
   if (leader) {
     mbar_init(bar_ld, 1);
-    mbar_init(bar_mma, 1);
+    mbar_init(bar_mma, 3);
     mbar_fence_init();
   }
   fence_async_smem();
@@ -356,6 +358,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = ts->tmem;
+  const bool issuer = lane == 0 && w < 3;          // issues accumulator group w
   if (leader) load_operands(opb, blob, L::BLOB, bar_ld);
   bool ok = __syncthreads_and(tc_wait(bar_ld, 0)) != 0;
   uint32_t phase = 0;
@@ -375,9 +378,9 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 
   // MMAs are issued only while ok (block-uniform), so every issued pass is waited for
   auto issue = [&](int p) {
-    if (leader && ok) {
+    if (issuer && ok) {
       fence_after_sync();
-      issue_pass(tmem, CS, opa_s, L::OPA_SPLIT, KPA, opb_s + (uint32_t)L::off(p), L::np(p), L::kp(p), bar_mma);
+      issue_group(w, tmem, CS, opa_s, L::OPA_SPLIT, KPA, opb_s + (uint32_t)L::off(p), L::np(p), L::kp(p), bar_mma);
     }
   };
   auto wait_pass = [&]() {
@@ -617,7 +620,7 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
   if (w == 0) tmem_alloc<NCOLS>(ts);
   if (leader) {
     mbar_init(bar_ld, 1);
-    mbar_init(bar_mma, 1);
+    mbar_init(bar_mma, 3);
     mbar_fence_init();
   }
   fence_async_smem();
@@ -625,6 +628,7 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = ts->tmem;
+  const bool issuer = lane == 0 && w < 3;
   if (leader) load_operands(opb, blob, L::BLOB_N, bar_ld);
   bool ok = __syncthreads_and(tc_wait(bar_ld, 0)) != 0;
   uint32_t phase = 0;
@@ -726,9 +730,9 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
     fence_async_smem();
     fence_before_sync();
     __syncthreads();
-    if (leader && ok) {
+    if (issuer && ok) {
       fence_after_sync();
-      issue_pass(tmem, NPL, opa_s, L::OPN_SPLIT, KPN, opb_s, NPL, KPN, bar_mma);
+      issue_group(w, tmem, NPL, opa_s, L::OPN_SPLIT, KPN, opb_s, NPL, KPN, bar_mma);
     }
     const bool was_ok = ok;
     const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
