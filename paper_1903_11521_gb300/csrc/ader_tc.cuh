@@ -237,6 +237,29 @@ __device__ __forceinline__ void tmem_ld3x8(uint32_t a0, uint32_t a1, uint32_t a2
   for (int i = 0; i < 24; ++i) r[i / 8][i % 8] = __uint_as_float(u[i]);
 }
 
+// 3 x 8 accumulator columns without waiting: the values are valid only after tmem_wait24
+// (which takes the registers as operands, so no use can move above it).
+__device__ __forceinline__ void tmem_ld3x8_async(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t (&u)[24]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23])
+      : "r"(a0), "r"(a1), "r"(a2)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait24(uint32_t (&u)[24]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]), "+r"(u[6]), "+r"(u[7]),
+                 "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]),
+                 "+r"(u[15]), "+r"(u[16]), "+r"(u[17]), "+r"(u[18]), "+r"(u[19]), "+r"(u[20]), "+r"(u[21]),
+                 "+r"(u[22]), "+r"(u[23])
+               :
+               : "memory");
+}
+
 // Stores 8 K-consecutive values of one operand row as hi and lo bf16 parts.
 __device__ __forceinline__ void store_split8(unsigned char* op, int split_bytes, int off, const float (&v)[8]) {
   uint32_t hi[4], lo[4];
@@ -423,14 +446,20 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         }
   };
   // 3 x 8 accumulator columns (plane stride r8) of this thread's lane into xs
-  auto stage_chunk = [&](int col0, int r8) {
-    float r[3][8];
-    tmem_ld3x8(my_tmem + col0, my_tmem + col0 + r8, my_tmem + col0 + 2 * r8, r);
+  // accumulator chunks: columns col0 + x * r8 + 0..7 (x = 0..2) of this thread's lane;
+  // the load of chunk c + 1 is issued before chunk c is mixed and waited for after it
+  auto load_chunk = [&](int col0, int r8, uint32_t (&u)[24]) {
+    tmem_ld3x8_async(my_tmem + col0, my_tmem + col0 + r8, my_tmem + col0 + 2 * r8, u);
+  };
+  auto put_chunk = [&](uint32_t (&u)[24]) {
+    tmem_wait24(u);
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       float4* dst = reinterpret_cast<float4*>(xs) + ((x * kNq + w) * 2) * kTile + lane;
-      dst[0] = make_float4(r[x][0], r[x][1], r[x][2], r[x][3]);
-      dst[kTile] = make_float4(r[x][4], r[x][5], r[x][6], r[x][7]);
+      dst[0] = make_float4(__uint_as_float(u[8 * x]), __uint_as_float(u[8 * x + 1]),
+                           __uint_as_float(u[8 * x + 2]), __uint_as_float(u[8 * x + 3]));
+      dst[kTile] = make_float4(__uint_as_float(u[8 * x + 4]), __uint_as_float(u[8 * x + 5]),
+                               __uint_as_float(u[8 * x + 6]), __uint_as_float(u[8 * x + 7]));
     }
   };
 
@@ -444,16 +473,18 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       for (int s = 0; s < 3; ++s)
         sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : 0.0f;
 
-    // D~^0 = Q as operand
-    static_for<0, up8(B) / 8>([&](auto cc) {
-      constexpr int k0 = decltype(cc)::value * 8;
-      float v[8];
+    // D~^0 = Q as operand (two chunks of loads in flight at a time)
+    static_for<0, (up8(B) / 8 + 1) / 2>([&](auto cc) {
+      constexpr int k0 = decltype(cc)::value * 16;
+      float v[16];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < 16; ++i) {
         const int k = k0 + i;
         v[i] = k < B ? (float)__ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0f;
       }
-      store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+      store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), *reinterpret_cast<float(*)[8]>(v));
+      if constexpr (k0 + 8 < up8(B))
+        store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0 + 8, KPA), *reinterpret_cast<float(*)[8]>(v + 8));
     });
     sync_for_mma();
     issue(0);
@@ -463,41 +494,60 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       constexpr int DELTA = decltype(dd)::value;
       constexpr int R = Dm::nd(DELTA + 1), R8 = up8(R);
       wait_pass();
+      uint32_t ua[24], ub[24];       // chunk c in ua (c even) or ub (c odd)
+      load_chunk(0, R8, ua);
       static_for<0, R8 / 8>([&](auto cc) {
-        constexpr int k0 = decltype(cc)::value * 8;
-        stage_chunk(k0, R8);
-        __syncthreads();
-        float v[8];
-        mix_star(sc, v);
+        constexpr int c = decltype(cc)::value, k0 = c * 8;
+        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24]) {
+          put_chunk(cur);
+          if constexpr (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
+          __syncthreads();
+          float v[8];
+          mix_star(sc, v);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int k = k0 + i;
-          if (k < R) {
-            v[i] *= (float)dt;
-            my_scr[(tc_srow<N>(DELTA + 1) + k) * kRows] = v[i];
-          } else {
-            v[i] = 0.0f;
+          for (int i = 0; i < 8; ++i) {
+            const int k = k0 + i;
+            if (k < R) {
+              v[i] *= (float)dt;
+              my_scr[(tc_srow<N>(DELTA + 1) + k) * kRows] = v[i];
+            } else {
+              v[i] = 0.0f;
+            }
           }
-        }
-        store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
-        sync_for_mma();
+          store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+          if constexpr (k0 + 8 < R8) __syncthreads();
+        };
+        if constexpr (c % 2 == 0) body(ua, ub);
+        else body(ub, ua);
       });
+      sync_for_mma();
       if constexpr (DELTA + 1 < N) issue(DELTA + 1);
     });
 
-    // time integral I = sum_d (dt / (d+1)!) D~^d in binary64: HBM and operand
+    // time integral I = sum_d (dt / (d+1)!) D~^d in binary64: HBM and operand.  All loads
+    // of a chunk are issued before its stores (a store to I could alias them otherwise,
+    // which serialises every row on the L2 latency).
     double* It = Iout + tile * (kNq * B * kTile);
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
+      double qv[8];
+      float sv[N][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        qv[i] = (k0 + i < B) ? Qt[(w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane] : 0.0;
+#pragma unroll
+        for (int d = 1; d <= N; ++d)
+          sv[d - 1][i] = (k0 + i < Dm::nd(d)) ? my_scr[(tc_srow<N>(d) + k0 + i) * kRows] : 0.0f;
+      }
       float v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int k = k0 + i;
         if (k < B) {
-          double ik = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+          double ik = dt * T.invfact[0] * qv[i];
 #pragma unroll
           for (int d = 1; d <= N; ++d)
-            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], (double)my_scr[(tc_srow<N>(d) + k) * kRows], ik);
+            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], (double)sv[d - 1][i], ik);
           It[(w * B + k) * kTile + lane] = ik;
           v[i] = (float)ik;
         } else {
@@ -514,28 +564,50 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       constexpr int V = decltype(vv)::value;
       constexpr int R = L::vrows(V), R8 = up8(R), KB0 = V * L::VR;
       wait_pass();
-      static_for<0, R8 / 8>([&](auto cc) {
-        constexpr int k0 = decltype(cc)::value * 8;
-        stage_chunk(k0, R8);
-        __syncthreads();
-        float v[8];
-        mix_star(sc, v);
+      uint32_t ua[24], ub[24];
+      double qa[8], qb[8];           // Q of chunk c in qa (c even) or qb (c odd), loaded one chunk ahead
+      load_chunk(0, R8, ua);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int k = KB0 + k0 + i;
-          if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + (double)v[i];
-        }
-        fence_before_sync();
-        __syncthreads();
+      for (int i = 0; i < 8; ++i) qa[i] = (i < R) ? Qt[(w * B + KB0 + (i < R ? i : 0)) * kTile + lane] : 0.0;
+      static_for<0, R8 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value, k0 = c * 8;
+        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24], double (&qc)[8], double (&qn)[8]) {
+          put_chunk(cur);
+          if constexpr (k0 + 8 < R8) {
+            load_chunk(k0 + 8, R8, nxt);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              qn[i] = (k0 + 8 + i < R) ? Qt[(w * B + KB0 + (k0 + 8 + i < R ? k0 + 8 + i : 0)) * kTile + lane] : 0.0;
+          }
+          __syncthreads();
+          float v[8];
+          mix_star(sc, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = KB0 + k0 + i;
+            if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = qc[i] + (double)v[i];
+          }
+          if constexpr (k0 + 8 < R8) __syncthreads();
+        };
+        if constexpr (c % 2 == 0) body(ua, ub, qa, qb);
+        else body(ub, ua, qb, qa);
       });
+      fence_before_sync();
+      __syncthreads();
       if constexpr (V + 1 < NV) issue(N + V + 1);
       else issue(N + NV);
     });
 
     // face projections P^s = R^sT I -> Pface; local flux products W = P^s Aloc_s^T -> Wloc
+    // (the flux-solver rows of all four faces are loaded while the pass runs)
+    const float* Ft = floc + tile * (4 * kNq * kNq * kTile);
+    float af[4][kNq];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int q = 0; q < kNq; ++q) af[f][q] = __ldg(Ft + ((f * kNq + w) * kNq + q) * kTile + lane);
     wait_pass();
     float* Pe = Pface + (tile * kTile + lane) * (4 * kNq * BT8);
-    const float* Ft = floc + tile * (4 * kNq * kNq * kTile);
     float* Wt = Wloc + tile * (4 * kNq * BT * kTile);
     static_for<0, 4>([&](auto face) {
       constexpr int s = decltype(face)::value;
@@ -550,9 +622,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         dst[0] = make_float4(r[0], r[1], r[2], r[3]);
         dst[kTile] = make_float4(r[4], r[5], r[6], r[7]);
       });
-      float a[kNq];
-#pragma unroll
-      for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
+      const float (&a)[kNq] = af[s];
       __syncthreads();
       static_for<0, BT8 / 8>([&](auto cc) {
         constexpr int c = decltype(cc)::value;
