@@ -156,3 +156,56 @@ def test_zero_elements_is_a_no_op(yt):
     plan.execute({'X': y, 'Y': y}, 0)
     torch.cuda.synchronize()
     assert (y == 3.0).all()
+
+
+def test_lina_kernels_as_expressions(yt):
+    """The LinA (ADER-DG-SEM, 3D linearised acoustics, Sec. 5.2) kernels as expressions:
+    tensor-product CK derivative, volume, boundary-node extraction and the flux of one
+    pair of sides, with global 1D matrices, sparse 4 x 4 Jacobians (constant material on a
+    uniform mesh) and per-element DOF tensors, against the brute-force Eq. gentensorop."""
+    rng = np.random.default_rng(21)
+    n, E = 4, 11                                   # N + 1 nodes per direction
+    Kt, Kh = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    # acoustic Jacobians, q = (pressure, u, v, w): A couples p-u, B p-v, C p-w
+    jac = []
+    for d in range(3):
+        M = np.zeros((4, 4))
+        M[0, d + 1] = rng.uniform(1, 2)
+        M[d + 1, 0] = rng.uniform(1, 2)
+        jac.append(M)
+    As, Bs, Cs = jac
+    Ap, Am = rng.standard_normal((4, 4)), rng.standard_normal((4, 4))
+    Fs = np.zeros(n)
+    Fs[n - 1] = 1.0                                # F^sigma_i = delta_iN (right/top/front)
+    Fh = rng.standard_normal(n)
+    D0 = rng.standard_normal((E, n, n, n, 4))
+    consts = {'Kt': (Kt, None), 'As': (As, As != 0), 'Bs': (Bs, Bs != 0), 'Cs': (Cs, Cs != 0)}
+    out, plan = run(yt, "D1[xyzp] = Kt[xl] * D0[lyzq] * As[pq] + Kt[ym] * D0[xmzq] * Bs[pq]"
+                        " + Kt[zn] * D0[xynq] * Cs[pq]", consts, {'D0': D0}, 'D1', (n, n, n, 4), E)
+    assert plan.stats()['n_terms'] == 3
+    for e in (0, E - 1):
+        ref = (es.einsum_bruteforce('xyzp', [('xl', Kt), ('lyzq', D0[e]), ('pq', As)]) +
+               es.einsum_bruteforce('xyzp', [('ym', Kt), ('xmzq', D0[e]), ('pq', Bs)]) +
+               es.einsum_bruteforce('xyzp', [('zn', Kt), ('xynq', D0[e]), ('pq', Cs)]))
+        assert np.allclose(out[e], ref, rtol=1e-13, atol=1e-12 * np.abs(ref).max())
+    # volume: Q* = Q + Khat terms on the time integral
+    I = rng.standard_normal((E, n, n, n, 4))
+    Q = rng.standard_normal((E, n, n, n, 4))
+    consts = {'Kh': (Kh, None), 'As': (As, As != 0), 'Bs': (Bs, Bs != 0), 'Cs': (Cs, Cs != 0)}
+    out, _ = run(yt, "Qs[xyzp] += Kh[xl] * I[lyzq] * As[pq] + Kh[ym] * I[xmzq] * Bs[pq]"
+                     " + Kh[zn] * I[xynq] * Cs[pq]", consts, {'I': I}, 'Qs', (n, n, n, 4), E, out_init=Q)
+    ref = Q + (np.einsum('xl,elyzq,pq->exyzp', Kh, I, As) + np.einsum('ym,exmzq,pq->exyzp', Kh, I, Bs)
+               + np.einsum('zn,exynq,pq->exyzp', Kh, I, Cs))
+    assert np.allclose(out, ref, rtol=1e-13, atol=1e-12 * np.abs(ref).max())
+    # boundary nodes of one side (a copy expressed as a product with a selection vector)
+    out_z, _ = run(yt, "Z[xyp] = F[n] * I[xynp]", {'F': (Fs, Fs != 0)}, {'I': I}, 'Z', (n, n, 4), E)
+    assert np.array_equal(out_z, I[:, :, :, n - 1, :])
+    # flux of the side pair in z: own boundary nodes with A+, the neighbour's with A-
+    Zn = np.roll(out_z, 1, axis=0)                 # neighbour of element e: e - 1
+    consts = {'Fh': (Fh, None), 'Ap': (Ap, None), 'Am': (Am, None)}
+    out, _ = run(yt, "Qn[xyzp] += Fh[z] * Z[xyq] * Ap[pq] + Fh[z] * Zn[xyq] * Am[pq]", consts,
+                 {'Z': out_z, 'Zn': Zn}, 'Qn', (n, n, n, 4), E, out_init=Q)
+    for e in (0, 5):
+        ref = Q[e] + es.einsum_bruteforce('xyzp', [('z', Fh), ('xyq', out_z[e]), ('pq', Ap)]) + \
+            es.einsum_bruteforce('xyzp', [('z', Fh), ('xyq', Zn[e]), ('pq', Am)])
+        assert np.allclose(out[e], ref, rtol=1e-13, atol=1e-12 * np.abs(ref).max())
