@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"07fb4cfc4f9df534": {6: (304.598272e6 + 752.867328e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"6a69df252c6680b5": {6: (304.958976e6 + 753.266688e6) / 40000}}
 
 
 def kernel_source_digest(order=6, precision="f64"):

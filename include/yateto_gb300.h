@@ -316,6 +316,14 @@ void yt_server_destroy(struct yt_server* server);
  * (n/8)*16K + (k/8)*128 + (n%8)*16 + (k%8)*2.  `bytes` receives the size; pass out == NULL
  * to query it.  No counterpart in the paper. */
 yt_status yt_tc_operands(int32_t order, int32_t kernel, unsigned char* out, int64_t* bytes);
+/* Diagnostics: checks on the current device the integer-unit binary32 <-> binary64
+ * conversions used by the reduced-precision kernels against the hardware conversions:
+ * all 2^32 binary32 values (widening, exact; a subnormal input must give the signed
+ * zero) and 2^28 binary64 values with one in eight a rounding tie (narrowing, round to
+ * nearest even; a result the hardware rounds to a subnormal float counts as correct when
+ * ours is the signed zero).  Writes the numbers of
+ * mismatches; synchronous.  No counterpart in the paper. */
+yt_status yt_selftest_conversions(int64_t* f2d_mismatches, int64_t* d2f_mismatches);
 /* Host-only: reference matrices for an order without creating a solver (same meaning as
  * yt_solver_reference_matrix).  Runs no device code. */
 yt_status yt_reference_matrix(int32_t order, const char* name, double* out, int64_t* count);

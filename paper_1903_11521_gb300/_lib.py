@@ -91,6 +91,7 @@ SIGNATURES = {
     "yt_server_destroy": (None, [_P]),
     "yt_reference_matrix": (C.c_int, [C.c_int32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "yt_tc_operands": (C.c_int, [C.c_int32, C.c_int32, _P, C.POINTER(C.c_int64)]),
+    "yt_selftest_conversions": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 

@@ -35,7 +35,35 @@
 
 #include <type_traits>
 
+#include "fp_convert.cuh"
+
 namespace yt {
+
+// Conversions between the contraction type and binary64: identities for double; for
+// float either the hardware conversions or the integer-unit ones of fp_convert.cuh (INT),
+// which leave the FP64 pipe (the scarce resource of these kernels' binary64 parts) to the
+// arithmetic but cost registers: the kernels use them where they compile without spills.
+template <typename Real, bool INT>
+__device__ __forceinline__ double to_f64(Real x) {
+  if constexpr (sizeof(Real) == 4 && INT) return f2d_int(x);
+  else return (double)x;
+}
+template <typename Real, bool INT>
+__device__ __forceinline__ Real from_f64(double x) {
+  if constexpr (sizeof(Real) == 4 && INT) return d2f_int(x);
+  else return (Real)x;
+}
+
+// Resident CTAs per SM requested from the compiler (__launch_bounds__): the FP64 kernels
+// run one 9-warp CTA per SM (168 registers); the FP32 neighbour kernels and the FP32
+// local kernels of degree <= 4 fit 96 registers without spilling and run two CTAs per SM
+// (18 warps) to hide shared-memory and dependency latency.
+template <int N, typename Real, bool LOCAL>
+struct MinBlocks {
+  static constexpr int value = (sizeof(Real) == 4 && (!LOCAL || N <= 4)) ? 2 : 1;
+  // integer-unit conversions where they fit the registers (the two-CTA variants)
+  static constexpr bool int_cvt = value == 2;
+};
 
 namespace gen {
 // Row<N, LIST, ROW>::dot<Real>(v, x) = sum over the non-zeros (l, value offset o) of row
@@ -142,6 +170,7 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
     constexpr int nout = Dm::nd(DELTA + 1);
     constexpr int KC = Dm::KC;
     const Real* xcol = Dsh + w * kTile + lane;
+    const Real dtr = (Real)dt;
     static_for<0, (nout + KC - 1) / KC>([&](auto chunk) {
       constexpr int k0 = decltype(chunk)::value * KC;
       // X^x[k][q] = sum_l Ktilde^x_kl D[l][q]  (this thread: column q = w)
@@ -164,9 +193,10 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
 #pragma unroll
             for (int s = 0; s < 3; ++s)
               if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-          v *= (Real)dt;
+          v *= dtr;
           Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
-          Icol[k0 + kk] = fma(dt * T.invfact[DELTA + 1], (double)v, Icol[k0 + kk]);
+          Icol[k0 + kk] = fma(dt * T.invfact[DELTA + 1], to_f64<Real, MinBlocks<N, Real, true>::int_cvt>(v),
+                              Icol[k0 + kk]);
         }
       });
       __syncthreads();
@@ -174,15 +204,6 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
     ck_step<N, DELTA + 1, Real>(T, dt, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
   }
 }
-
-// Resident CTAs per SM requested from the compiler (__launch_bounds__): the FP64 kernels
-// run one 9-warp CTA per SM (168 registers); the FP32 neighbour kernels and the FP32
-// local kernels of degree <= 4 fit 96 registers without spilling and run two CTAs per SM
-// (18 warps) to hide shared-memory and dependency latency.
-template <int N, typename Real, bool LOCAL>
-struct MinBlocks {
-  static constexpr int value = (sizeof(Real) == 4 && (!LOCAL || N <= 4)) ? 2 : 1;
-};
 
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume and local flux of one tile of 32 elements.
@@ -203,6 +224,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
         const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
+  constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Dsh = reinterpret_cast<Real*>(smem_raw);  // B rows x 9 x 32
   Real* Xsh = Dsh + B * kNq * kTile;               // XR rows x 9 x 32
@@ -241,7 +263,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const double q = __ldg(Qt + (w * B + k) * kTile + lane);
-    Dsh[(k * kNq + w) * kTile + lane] = (Real)q;
+    Dsh[(k * kNq + w) * kTile + lane] = from_f64<Real, CVT>(q);
     if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
   }
   // (own column only is read before the first barrier)
@@ -252,7 +274,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const double ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
-    Dsh[(k * kNq + w) * kTile + lane] = (Real)ik;
+    Dsh[(k * kNq + w) * kTile + lane] = from_f64<Real, CVT>(ik);
     It[(w * B + k) * kTile + lane] = ik;
   }
 
@@ -284,7 +306,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
 #pragma unroll
           for (int s = 0; s < 3; ++s)
             if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + (double)v;
+        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v);
       }
     });
     __syncthreads();
@@ -320,7 +342,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
       const Real* wcol = Xsh + w * kTile + lane;
       static_for<0, B>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        Qo[(w * B + k) * kTile + lane] += (double)row_dot<N, 25 + s, k>(T.val, wcol);
+        Qo[(w * B + k) * kTile + lane] += to_f64<Real, CVT>(row_dot<N, 25 + s, k>(T.val, wcol));
       });
     } else {
       Real* Wt = Wloc + tile * (4 * kNq * BT * kTile);
@@ -448,11 +470,12 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   static_for<0, B>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     const Real* wcol = Wsh + w * kTile + lane;
-    double dq = (double)row_dot<N, 25, k>(T.val, wcol);
-    dq += (double)row_dot<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile);
-    dq += (double)row_dot<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile);
-    dq += (double)row_dot<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile);
-    Qt[(w * B + k) * kTile + lane] += dq;
+    // the four faces' lifted rows summed in the contraction type, then one binary64 update
+    Real dq = row_dot<N, 25, k>(T.val, wcol);
+    dq += row_dot<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile);
+    dq += row_dot<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile);
+    dq += row_dot<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile);
+    Qt[(w * B + k) * kTile + lane] += to_f64<Real, MinBlocks<N, Real, false>::int_cvt>(dq);
   });
 }
 

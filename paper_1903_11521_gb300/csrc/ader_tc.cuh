@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "ader_kernels.cuh"
+#include "fp_convert.cuh"
 
 namespace yt {
 namespace tc {
@@ -129,6 +130,9 @@ struct Layout {
   static constexpr int BLOB_N = 2 * NPL * KPN * 2;
   static constexpr int STAGE_FLOATS = BT8 * kNq * kTile;     // one face of gathered projections
   static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 3 * STAGE_FLOATS * 4 + 64;
+  // k_local_tc converts with the integer units (fp_convert.cuh) except at degree 5, where
+  // the extra registers cost more than the FP64-pipe slots they save (measured)
+  static constexpr bool INT_CVT_LOCAL = N <= 4;
   static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
   static_assert(BT8 / 8 <= 3, "face basis too large for the exchange buffer");
 };
@@ -398,6 +402,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 #pragma unroll
   for (int s = 0; s < 3; ++s) scol[s] = (s < cnt) ? SP.col[s0 + s] : 0;
   const double dt = T.dt;
+  const float dtf = (float)dt;
 
   // MMAs are issued only while ok (block-uniform), so every issued pass is waited for
   auto issue = [&](int p) {
@@ -480,7 +485,8 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int k = k0 + i;
-        v[i] = k < B ? (float)__ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0f;
+        v[i] = k < B ? from_f64<float, L::INT_CVT_LOCAL>(__ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane))
+                     : 0.0f;
       }
       store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), *reinterpret_cast<float(*)[8]>(v));
       if constexpr (k0 + 8 < up8(B))
@@ -508,7 +514,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
           for (int i = 0; i < 8; ++i) {
             const int k = k0 + i;
             if (k < R) {
-              v[i] *= (float)dt;
+              v[i] *= dtf;
               my_scr[(tc_srow<N>(DELTA + 1) + k) * kRows] = v[i];
             } else {
               v[i] = 0.0f;
@@ -547,9 +553,9 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
           double ik = dt * T.invfact[0] * qv[i];
 #pragma unroll
           for (int d = 1; d <= N; ++d)
-            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], (double)sv[d - 1][i], ik);
+            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], to_f64<float, L::INT_CVT_LOCAL>(sv[d - 1][i]), ik);
           It[(w * B + k) * kTile + lane] = ik;
-          v[i] = (float)ik;
+          v[i] = from_f64<float, L::INT_CVT_LOCAL>(ik);
         } else {
           v[i] = 0.0f;
         }
@@ -585,7 +591,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int k = KB0 + k0 + i;
-            if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = qc[i] + (double)v[i];
+            if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]);
           }
           if constexpr (k0 + 8 < R8) __syncthreads();
         };
@@ -820,7 +826,7 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
       tmem_ld8(my_tmem + k0, r);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        if (k0 + i < B) Qt[(w * B + k0 + i) * kTile + lane] += (double)r[i];
+        if (k0 + i < B) Qt[(w * B + k0 + i) * kTile + lane] += f2d_int(r[i]);
     });
     fence_before_sync();
     __syncthreads();
