@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"6a69df252c6680b5": {6: (304.958976e6 + 753.266688e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"c84d8db34eb1531f": {6: (304.815360e6 + 754.947072e6) / 40000}}
 
 
 def kernel_source_digest(order=6, precision="f64"):
@@ -291,6 +291,23 @@ def form_precision(yt, order, E, steps, stream, precision="f32"):
     return out
 
 
+def form_local_update(yt, order, E, steps, stream):
+    """Local update alone (derivatives, time integral, volume, local flux; no neighbour
+    flux) of a small mesh: order 4, 1,000 tets, FP64, N(0,1) DOFs."""
+    N = order - 1
+    B = order * (order + 1) * (order + 2) // 6
+    el = wl.random_elements(E, seed=wl.SEED + 700)
+    Q = wl.random_dofs(E, B, seed=wl.SEED + 701)
+    dt = wl.cfl_time_step(el, N)
+    s = yt.Solver(order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, stream=stream)
+    s.set_dofs_host(Q, stream=stream)
+    ms = _timed(lambda: s.step_local(stream=stream), steps, 10, stream)
+    s.close()
+    return {"workload": f"local update (CK, time integral, volume, local flux), order {order}, "
+                        f"{E} tets, FP64, one CTA per 32 tets ({(E + 31) // 32} CTAs: launch-latency bound)",
+            "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms}
+
+
 def form_batching(yt, E, precision, lo, hi, steps, stream):
     rng = np.random.default_rng(wl.SEED + 600)
     orders = rng.integers(lo, hi + 1, E).astype(np.int8)
@@ -421,6 +438,7 @@ def run_ours(args):
     total_ms = ev[0][0].elapsed_time(ev[K - 1][2])
     local_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
     neigh_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    step_ms = sorted(e[0].elapsed_time(e[2]) for e in ev)
     t_max = total_ms
     if ws > 1:
         import torch.distributed as dist
@@ -491,7 +509,8 @@ def run_ours(args):
                          f"({t_s:.1f} s), dense unfactorised FP64 oracle"}
     forms = None
     if not args.no_forms and ws == 1:
-        forms = {"precision_o6": form_precision(yt, 6, E, 5, stream),
+        forms = {"local_update_o4_1000": form_local_update(yt, 4, 1000, 200, stream),
+                 "precision_o6": form_precision(yt, 6, E, 5, stream),
                  "precision_o6_bf16x3": form_precision(yt, 6, E, 5, stream, "bf16x3"),
                  "precision_o7": form_precision(yt, 7, E, 5, stream),
                  "batching_fp32": form_batching(yt, 2 * E, yt.YT_F32, 3, 7, 5, stream),
@@ -506,6 +525,7 @@ def run_ours(args):
             "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
             "gpu_launches": 2 * K,
             "kernel_ms": {"k_local": local_ms, "k_neigh": neigh_ms},
+            "step_ms_min_median": [step_ms[0], step_ms[len(step_ms) // 2]],
             "context": {"paper_skx_dp_o6_element_updates_per_s": 1244e6 / (56 * 9),
                         "paper_hardware": "2x Xeon Platinum 8174 (SKX), App. A"}}
     print(json.dumps(line), flush=True)

@@ -122,6 +122,15 @@ def emit_rows(N, lst, nvals):
                              for i in range(0, len(terms), 2)]
                 lines.append(f"    return {terms[0]};")
             lines.append("  }")
+            # one accumulator continuing from `a` (FP64: the pipe, not latency, is the
+            # limit, and every extra accumulator costs an add to combine)
+            lines.append("  template <typename R>")
+            lines.append("  static __device__ __forceinline__ R dot1(const R* __restrict__ v, "
+                         "const R* __restrict__ x, R a) {")
+            for c, voff in row:
+                lines.append(f"    a = fma(__ldg(v + {voff}), x[{c * ROW_STRIDE}], a);")
+            lines.append("    return a;")
+            lines.append("  }")
             if N <= CONST_MAX_N:
                 lines.append("  static __device__ __forceinline__ float dotc(const float* __restrict__ x) {")
                 if not row:

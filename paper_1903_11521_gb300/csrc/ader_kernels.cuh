@@ -74,14 +74,26 @@ template <int N, int LIST, int ROW>
 struct Row;
 }  // namespace gen
 
-// Sparse row of a list: FP32 values of degrees <= 5 come from constant memory
-// (Row::dotc, one constant-bank operand per fma), otherwise from the value array.
+// Sparse row of a list.  FP64: one accumulator chain (Row::dot1; the FP64 pipe is the
+// limit and nine warps supply enough independent chains, while every extra accumulator
+// costs an add to combine).  FP32: four accumulators (Row::dot; latency is the limit),
+// values of degrees <= 5 from constant memory (Row::dotc, one constant-bank operand per
+// fma).  row_dot_acc continues an accumulation (one chain across several rows in FP64).
 template <int N, int LIST, int ROW, typename Real>
 __device__ __forceinline__ Real row_dot(const Real* __restrict__ v, const Real* __restrict__ x) {
-  if constexpr (sizeof(Real) == 4 && N <= 5)
+  if constexpr (sizeof(Real) == 8)
+    return gen::Row<N, LIST, ROW>::dot1(v, x, Real(0));
+  else if constexpr (N <= 5)
     return gen::Row<N, LIST, ROW>::dotc(x);
   else
     return gen::Row<N, LIST, ROW>::dot(v, x);
+}
+template <int N, int LIST, int ROW, typename Real>
+__device__ __forceinline__ Real row_dot_acc(const Real* __restrict__ v, const Real* __restrict__ x, Real a) {
+  if constexpr (sizeof(Real) == 8)
+    return gen::Row<N, LIST, ROW>::dot1(v, x, a);
+  else
+    return a + row_dot<N, LIST, ROW, Real>(v, x);
 }
 
 template <int Begin, int End, typename F>
@@ -470,11 +482,12 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   static_for<0, B>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     const Real* wcol = Wsh + w * kTile + lane;
-    // the four faces' lifted rows summed in the contraction type, then one binary64 update
+    // the four faces' lifted rows summed in the contraction type (FP64: one chain), then
+    // one binary64 update
     Real dq = row_dot<N, 25, k>(T.val, wcol);
-    dq += row_dot<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile);
-    dq += row_dot<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile);
-    dq += row_dot<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile);
+    dq = row_dot_acc<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile, dq);
+    dq = row_dot_acc<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile, dq);
+    dq = row_dot_acc<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile, dq);
     Qt[(w * B + k) * kTile + lane] += to_f64<Real, MinBlocks<N, Real, false>::int_cvt>(dq);
   });
 }
