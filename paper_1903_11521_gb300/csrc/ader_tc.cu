@@ -141,8 +141,6 @@ void launch_neigh(const tc::TcLaunch& L, int variant) {
     default: throw Error(YT_ERR_UNSUPPORTED, "tensor-core step: orders 2..6"); \
   }
 
-bool tc_supported(int N) { return N >= 1 && N <= 5; }
-
 size_t tc_smem_local(int N) {
   size_t r = 0;
 #define YT_C(n) r = tc::Layout<n>::SMEM

@@ -225,22 +225,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&r)[8]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) r[i] = __uint_as_float(u[i]);
 }
-__device__ __forceinline__ void tmem_ld3x8(uint32_t a0, uint32_t a1, uint32_t a2, float (&r)[3][8]) {
-  uint32_t u[24];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
-        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23])
-      : "r"(a0), "r"(a1), "r"(a2)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 24; ++i) r[i / 8][i % 8] = __uint_as_float(u[i]);
-}
-
 // 3 x 8 accumulator columns without waiting: the values are valid only after tmem_wait24
 // (which takes the registers as operands, so no use can move above it).
 __device__ __forceinline__ void tmem_ld3x8_async(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t (&u)[24]) {
@@ -865,7 +849,6 @@ struct TcLaunch {
 size_t tc_smem_local(int N);
 size_t tc_smem_neigh(int N);
 size_t tc_scratch_floats(int N, unsigned grid);
-bool tc_supported(int N);
 void tc_operands_local(int N, std::vector<unsigned char>& out);
 void tc_operands_neigh(int N, std::vector<unsigned char>& out);
 void tc_set_attributes(int N);
