@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"c84d8db34eb1531f": {6: (304.815360e6 + 754.947072e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"7d171a0cd67e30dc": {6: (303.124992e6 + 752.771072e6) / 40000}}
 
 
 def kernel_source_digest(order=6, precision="f64"):

@@ -131,6 +131,41 @@ def emit_rows(N, lst, nvals):
                 lines.append(f"    a = fma(__ldg(v + {voff}), x[{c * ROW_STRIDE}], a);")
             lines.append("    return a;")
             lines.append("  }")
+            # the same two forms with the operand column in a register array x[0..S)
+            lines.append("  template <typename R, int S>")
+            lines.append("  static __device__ __forceinline__ R dotr1(const R* __restrict__ v, "
+                         "const R (&x)[S], R a) {")
+            for c, voff in row:
+                lines.append(f"    a = fma(__ldg(v + {voff}), x[{c}], a);")
+            lines.append("    return a;")
+            lines.append("  }")
+            # operand rows c < S in the register array, rows c >= S in shared memory
+            lines.append("  template <typename R, int S>")
+            lines.append("  static __device__ __forceinline__ R dotrh(const R* __restrict__ v, "
+                         "const R (&xr)[S], const R* __restrict__ xs, R a) {")
+            for c, voff in row:
+                lines.append(f"    a = fma(__ldg(v + {voff}), ({c} < S) ? xr[({c} < S) ? {c} : 0] : "
+                             f"xs[({c} - S) * {ROW_STRIDE}], a);")
+            lines.append("    return a;")
+            lines.append("  }")
+            if N <= CONST_MAX_N:
+                lines.append("  template <int S>")
+                lines.append("  static __device__ __forceinline__ float dotrc(const float (&x)[S]) {")
+                if not row:
+                    lines.append("    return 0.0f;")
+                else:
+                    na = min(N_ACC, len(row))
+                    for a in range(na):
+                        lines.append(f"    float a{a} = 0.0f;")
+                    for i, (c, voff) in enumerate(row):
+                        a = i % na
+                        lines.append(f"    a{a} = fmaf(c_vals_o{N}[{voff}], x[{c}], a{a});")
+                    terms = [f"a{a}" for a in range(na)]
+                    while len(terms) > 1:
+                        terms = [f"({terms[i]} + {terms[i + 1]})" if i + 1 < len(terms) else terms[i]
+                                 for i in range(0, len(terms), 2)]
+                    lines.append(f"    return {terms[0]};")
+                lines.append("  }")
             if N <= CONST_MAX_N:
                 lines.append("  static __device__ __forceinline__ float dotc(const float* __restrict__ x) {")
                 if not row:

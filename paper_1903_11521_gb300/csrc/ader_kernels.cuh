@@ -96,6 +96,15 @@ __device__ __forceinline__ Real row_dot_acc(const Real* __restrict__ v, const Re
     return a + row_dot<N, LIST, ROW, Real>(v, x);
 }
 
+// The same with the operand column in a register array x[0..S).
+template <int N, int LIST, int ROW, typename Real, int S>
+__device__ __forceinline__ Real row_dotr(const Real* __restrict__ v, const Real (&x)[S]) {
+  if constexpr (sizeof(Real) == 4 && N <= 5)
+    return gen::Row<N, LIST, ROW>::dotrc(x);
+  else
+    return gen::Row<N, LIST, ROW>::template dotr1<Real, S>(v, x, Real(0));
+}
+
 template <int Begin, int End, typename F>
 __device__ __forceinline__ void static_for(F&& f) {
   if constexpr (Begin < End) {
@@ -166,32 +175,69 @@ struct TileRef {
   double dt;
 };
 
+// Where k_local keeps the operand column of its sparse products (D~^delta, then I): rows
+// in registers make every non-zero one fma with a register operand (the binary64
+// time-integral accumulator then lives in shared memory, touched once per row and
+// derivative); rows in shared memory cost one load per fma.
+// Rows of the operand column held in registers (the rest in shared memory).  The FP64
+// column of degree 5 (56 doubles) does not fit beside the rest of the kernel under the
+// 168-register cap of a 9-warp CTA: its C(N+2,3) = 35 rows of degree < 5 (read by every
+// list) are registers, its 21 rows of degree 5 (read only by the first derivative and the
+// face projections) shared memory.  Degree 6 in FP64 is not built.
+template <int N, typename Real>
+struct LocalRegRows {
+  static constexpr int value = (sizeof(Real) == 8 && N >= 5) ? Dims<N>::nd(1) : Dims<N>::B;
+};
+// Shared memory of k_local ([rows][9][32] each): operand rows not in registers, the
+// exchange buffer, and the binary64 time-integral accumulator when any operand row is
+// in registers (it is in registers otherwise).
+template <int N, typename Real>
+constexpr size_t local_smem_bytes() {
+  using Dm = Dims<N>;
+  constexpr int RS = LocalRegRows<N, Real>::value;
+  return (size_t)sizeof(Real) * (Dm::B - RS + Dm::XR) * kNq * kTile +
+         (RS > 0 ? (size_t)8 * Dm::nd(1) * kNq * kTile : 0);
+}
+// Sparse row with the operand column split at RS: rows < RS in D (registers), rows >= RS
+// in shared memory at xs (that part of this thread's column, stride 9 x 32).
+template <int N, int LIST, int ROW, int RS, typename Real, int S>
+__device__ __forceinline__ Real row_op(const Real* __restrict__ v, const Real (&D)[S], const Real* __restrict__ xs) {
+  if constexpr (RS == 0)
+    return row_dot<N, LIST, ROW, Real>(v, xs);
+  else if constexpr (RS >= Dims<N>::B)
+    return row_dotr<N, LIST, ROW, Real>(v, D);
+  else
+    return gen::Row<N, LIST, ROW>::template dotrh<Real, S>(v, D, xs, Real(0));
+}
+
 // ------------------------------------------------------------------- CK derivatives
 // One derivative step delta -> delta+1, in place in Dsh: output row k only reads rows of
 // strictly higher polynomial degree (K~_kl != 0 only if deg phi_k < deg phi_l), so rows
 // processed in increasing order overwrite rows that are no longer needed.  The time
 // integral accumulates in double registers; only the C(N+2,3) rows that receive
 // derivative terms need one (rows of degree N hold c0 Q alone).
-template <int N, int DELTA, typename Real>
+template <int N, int DELTA, typename Real, int RS, int S>
 __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, const int (&scol)[3], int cnt,
-                                        Real* __restrict__ Dsh, Real* __restrict__ Xsh,
+                                        Real* __restrict__ Dsh, Real (&D)[S], Real* __restrict__ Xsh,
                                         const Real (&sc)[3][3], double (&Icol)[Dims<N>::nd(1)],
-                                        int w, int lane) {
+                                        double* __restrict__ Ish, int w, int lane) {
   using Dm = Dims<N>;
   if constexpr (DELTA < N) {
     constexpr int nout = Dm::nd(DELTA + 1);
     constexpr int KC = Dm::KC;
+    constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
     const Real* xcol = Dsh + w * kTile + lane;
     const Real dtr = (Real)dt;
+    const double cw = dt * T.invfact[DELTA + 1];
     static_for<0, (nout + KC - 1) / KC>([&](auto chunk) {
       constexpr int k0 = decltype(chunk)::value * KC;
       // X^x[k][q] = sum_l Ktilde^x_kl D[l][q]  (this thread: column q = w)
       static_for<0, KC>([&](auto kkc) {
         constexpr int kk = decltype(kkc)::value;
         if constexpr (k0 + kk < nout) {
-          Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 0, k0 + kk>(T.val, xcol);
-          Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 1, k0 + kk>(T.val, xcol);
-          Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, DELTA * 3 + 2, k0 + kk>(T.val, xcol);
+          Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, DELTA * 3 + 0, k0 + kk, RS>(T.val, D, xcol);
+          Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, DELTA * 3 + 1, k0 + kk, RS>(T.val, D, xcol);
+          Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, DELTA * 3 + 2, k0 + kk, RS>(T.val, D, xcol);
         }
       });
       __syncthreads();
@@ -206,14 +252,20 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
             for (int s = 0; s < 3; ++s)
               if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
           v *= dtr;
-          Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
-          Icol[k0 + kk] = fma(dt * T.invfact[DELTA + 1], to_f64<Real, MinBlocks<N, Real, true>::int_cvt>(v),
-                              Icol[k0 + kk]);
+          if constexpr (RS > 0) {
+            static_assert(nout <= RS, "derivative rows must be register rows");
+            D[k0 + kk] = v;
+            double* ip = Ish + ((k0 + kk) * kNq + w) * kTile + lane;
+            *ip = fma(cw, to_f64<Real, CVT>(v), *ip);
+          } else {
+            Dsh[((k0 + kk) * kNq + w) * kTile + lane] = v;
+            Icol[k0 + kk] = fma(cw, to_f64<Real, CVT>(v), Icol[k0 + kk]);
+          }
         }
       });
       __syncthreads();
     });
-    ck_step<N, DELTA + 1, Real>(T, dt, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+    ck_step<N, DELTA + 1, Real, RS, S>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Icol, Ish, w, lane);
   }
 }
 
@@ -235,11 +287,15 @@ __global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value)
 k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
         const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
-  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
+  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC, XR = Dm::XR;
   constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
+  constexpr int RS = LocalRegRows<N, Real>::value;   // operand rows in registers
+  constexpr int SD = RS > 0 ? RS : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* Dsh = reinterpret_cast<Real*>(smem_raw);  // B rows x 9 x 32
-  Real* Xsh = Dsh + B * kNq * kTile;               // XR rows x 9 x 32
+  // [B - RS operand rows][XR exchange rows][NI accumulator rows (double), when RS > 0]
+  Real* Dsh = reinterpret_cast<Real*>(smem_raw);
+  Real* Xsh = Dsh + (B - RS) * kNq * kTile;
+  double* Ish = RS > 0 ? reinterpret_cast<double*>(Xsh + XR * kNq * kTile) : nullptr;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   size_t tile = blockIdx.x;
@@ -271,22 +327,34 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
       sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : Real(0);
 
   constexpr int NI = Dm::nd(1);
-  double Icol[NI];
+  Real D[SD];           // operand rows < RS
+  double Icol[NI];      // time-integral accumulator (RS == 0)
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const double q = __ldg(Qt + (w * B + k) * kTile + lane);
-    Dsh[(k * kNq + w) * kTile + lane] = from_f64<Real, CVT>(q);
-    if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
+    if (k < RS) D[k < RS ? k : 0] = from_f64<Real, CVT>(q);
+    else Dsh[((k - RS) * kNq + w) * kTile + lane] = from_f64<Real, CVT>(q);
+    if constexpr (RS > 0) {
+      if (k < NI) Ish[(k * kNq + w) * kTile + lane] = dt * T.invfact[0] * q;
+    } else {
+      if (k < NI) Icol[k < NI ? k : 0] = dt * T.invfact[0] * q;
+    }
   }
   // (own column only is read before the first barrier)
-  ck_step<N, 0, Real>(T, dt, scol, cnt, Dsh, Xsh, sc, Icol, w, lane);
+  const Real* xcol = Dsh + w * kTile + lane;      // this thread's shared operand rows
+  ck_step<N, 0, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Icol, Ish, w, lane);
 
-  // publish I: shared (own column) and HBM
+  // publish I: operand column (own) and HBM
   double* It = Iout + tile * (kNq * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    const double ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
-    Dsh[(k * kNq + w) * kTile + lane] = from_f64<Real, CVT>(ik);
+    double ik;
+    if constexpr (RS > 0)
+      ik = k < NI ? Ish[(k * kNq + w) * kTile + lane] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+    else
+      ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+    if (k < RS) D[k < RS ? k : 0] = from_f64<Real, CVT>(ik);
+    else Dsh[((k - RS) * kNq + w) * kTile + lane] = from_f64<Real, CVT>(ik);
     It[(w * B + k) * kTile + lane] = ik;
   }
 
@@ -296,15 +364,14 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   double* Qo = Qout + tile * (kNq * B * kTile);
 
   // volume: dQ[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q]
-  const Real* icol = Dsh + w * kTile + lane;
   static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
     constexpr int k0 = decltype(chunk)::value * KC;
     static_for<0, KC>([&](auto kkc) {
       constexpr int kk = decltype(kkc)::value;
       if constexpr (k0 + kk < B) {
-        Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 18, k0 + kk>(T.val, icol);
-        Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 19, k0 + kk>(T.val, icol);
-        Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_dot<N, 20, k0 + kk>(T.val, icol);
+        Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 18, k0 + kk, RS>(T.val, D, xcol);
+        Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 19, k0 + kk, RS>(T.val, D, xcol);
+        Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 20, k0 + kk, RS>(T.val, D, xcol);
       }
     });
     __syncthreads();
@@ -331,7 +398,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
     constexpr int s = decltype(face)::value;
     static_for<0, BT>([&](auto mm) {
       constexpr int m = decltype(mm)::value;
-      const Real z = row_dot<N, 21 + s, m>(T.val, icol);
+      const Real z = row_op<N, 21 + s, m, RS>(T.val, D, xcol);
       Xsh[(m * kNq + w) * kTile + lane] = z;
       Pt[(s * kNq + w) * BT + m] = z;
     });
@@ -521,6 +588,25 @@ StepTables<Real> step_tables(const AderLaunch& L) {
     T.invfact[i] = 1.0 / f;
   }
   return T;
+}
+
+// Shared memory of k_local for a runtime degree (1..6) and contraction type.
+inline size_t ader_local_smem(int N, bool f32) {
+  switch (N * 2 + (f32 ? 1 : 0)) {
+    case 2: return local_smem_bytes<1, double>();
+    case 3: return local_smem_bytes<1, float>();
+    case 4: return local_smem_bytes<2, double>();
+    case 5: return local_smem_bytes<2, float>();
+    case 6: return local_smem_bytes<3, double>();
+    case 7: return local_smem_bytes<3, float>();
+    case 8: return local_smem_bytes<4, double>();
+    case 9: return local_smem_bytes<4, float>();
+    case 10: return local_smem_bytes<5, double>();
+    case 11: return local_smem_bytes<5, float>();
+    case 12: return local_smem_bytes<6, double>();
+    case 13: return local_smem_bytes<6, float>();
+  }
+  return 0;
 }
 
 // Launch functions of one kernel variant (LOCAL: k_local<N, !FUSED>; else

@@ -254,7 +254,8 @@ void set_smem(yt_solver* s) {
   const int B = n_basis(N), BT = n_face_basis(N);
   const int KC = BT / 3 > 0 ? BT / 3 : 1;
   const int XR = 3 * KC > BT ? 3 * KC : BT;
-  s->smem_local = s->real_bytes * (size_t)(B + XR) * kNq * kTile;
+  (void)XR;
+  s->smem_local = ader_local_smem(N, s->prec != YT_F64);
   s->smem_neigh = s->real_bytes * (size_t)(4 * BT) * kNq * kTile;
   YT_REQUIRE(s->smem_local <= 227 * 1024 && s->smem_neigh <= 227 * 1024, YT_ERR_UNSUPPORTED,
              "order too high for this precision");
