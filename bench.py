@@ -20,6 +20,7 @@ import hashlib
 import json
 import multiprocessing as mp
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -43,20 +44,24 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic of k_local per element, keyed by the sha256 prefix of the kernel source
 # it was captured on (see profiles/k_local_o6_fp64_40k.md)
-NCU_TRAFFIC_PER_ELEMENT = {"7d171a0cd67e30dc": {6: (303.124992e6 + 752.771072e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"96733ca33e11455b": {6: (303.124992e6 + 752.771072e6) / 40000}}
 
 
 def kernel_source_digest(order=6, precision="f64"):
     """Digest of what the timed kernels of one order and contraction type are built from:
-    the kernel header and the generated rows and units of that degree."""
+    the kernel header and the generated rows and units of that degree, with comments and
+    blank space removed (a comment edit does not change the kernels)."""
     h = hashlib.sha256()
     n = order - 1
     pkg = os.path.join(ROOT, "paper_1903_11521_gb300")
-    files = [os.path.join(pkg, "csrc", "ader_kernels.cuh"),
+    files = [os.path.join(pkg, "csrc", "ader_kernels.cuh"), os.path.join(pkg, "csrc", "fp_convert.cuh"),
              os.path.join(pkg, "_build", "gen", f"yt_rows_o{n}.cuh")]
     files += [os.path.join(pkg, "_build", "gen", f"ader_o{n}_{precision}_{v}.cu") for v in ("lf", "nf")]
     for f in files:
-        h.update(open(f, "rb").read() if os.path.exists(f) else b"missing")
+        text = open(f).read() if os.path.exists(f) else "missing"
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

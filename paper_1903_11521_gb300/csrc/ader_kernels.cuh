@@ -20,9 +20,9 @@
 //
 // Sparse products with the global matrices are straight-line code generated per degree
 // (codegen.py): every non-zero of the list is one fma with its value read at a fixed
-// offset of the solver's value array and its operand at a fixed shared-memory offset, so
-// structural zeros and the equivalent-sparsity zero blocks (Sec. 4.2, 5.1.2) are never
-// multiplied:
+// offset of the solver's value array (FP32: of constant memory) and its operand a fixed
+// register or shared-memory element of the thread's operand column, so structural zeros
+// and the equivalent-sparsity zero blocks (Sec. 4.2, 5.1.2) are never multiplied:
 //   CK derivative delta: Ktilde^x restricted to rows < C(N-delta+2,3), columns
 //                        < C(N-delta+3,3) (the derivative staircase);
 //   volume:              Khat^x (zero columns l >= C(N+2,3) are absent);

@@ -235,8 +235,9 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
     }                                                                          \
   } while (0)
 
-// Shared memory of the two kernels of degree N: k_local holds the B-row column buffer
-// and the exchange buffer, k_neigh the four faces' flux products.
+// Shared memory of the two kernels of degree N: k_local holds the operand rows not kept
+// in registers, the exchange buffer and (with register operands) the time-integral
+// accumulator; k_neigh the four faces' flux products.
 void set_smem(yt_solver* s) {
   const int N = s->N;
   if (s->prec == YT_BF16X3_F32ACC) {
@@ -251,10 +252,7 @@ void set_smem(yt_solver* s) {
     cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
     return;
   }
-  const int B = n_basis(N), BT = n_face_basis(N);
-  const int KC = BT / 3 > 0 ? BT / 3 : 1;
-  const int XR = 3 * KC > BT ? 3 * KC : BT;
-  (void)XR;
+  const int BT = n_face_basis(N);
   s->smem_local = ader_local_smem(N, s->prec != YT_F64);
   s->smem_neigh = s->real_bytes * (size_t)(4 * BT) * kNq * kTile;
   YT_REQUIRE(s->smem_local <= 227 * 1024 && s->smem_neigh <= 227 * 1024, YT_ERR_UNSUPPORTED,
