@@ -256,3 +256,41 @@ def test_f32_order7_100_steps_against_oracle(yt):
     print(f"order 7 FP32 after 100 steps: {err:.3e} of the solution norm; "
           f"per quantity {np.array2string(rel_per_quantity(q32, Q), precision=2)}")
     assert err < 1e-4
+
+
+@pytest.mark.parametrize("prec_name, tol_inc", [("YT_F64", 1e-11), ("YT_F32", 2e-5), ("YT_BF16X3_F32ACC", 1e-3)])
+def test_single_element_self_neighbour(yt, prec_name, tol_inc):
+    """Degenerate connectivity: one element (one tile of 32 lanes with 31 padding lanes)
+    whose four faces are its own neighbours (faces paired 0-3 and 1-2, all orientations):
+    the neighbour flux reads the element's own face projections."""
+    order, N = 5, 4
+    el = wl.random_elements(1, seed=71)
+    Q = wl.random_dofs(1, basis.n_basis(N), seed=72, scale="impedance", elements=el)
+    dt = wl.cfl_time_step(el, N)
+    nbr = np.zeros((1, 4), dtype=np.int32)
+    faces = np.array([[3, 2, 1, 0]], dtype=np.int8)
+    orient = np.array([[0, 1, 2, 1]], dtype=np.int8)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    s = yt.Solver(order, dt, mat, el.jac, nbr, faces, orient, precision=getattr(yt, prec_name))
+    s.set_dofs_host(Q)
+    s.step()
+    s.status()
+    q = s.get_host()
+    s.close()
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    ref, _ = scheme.ader_step(Q, star, loc, nb, nbr, faces, orient, dt, N)
+    assert rel_per_quantity(q - Q, ref - Q).max() < tol_inc
+
+
+def test_zero_dofs_stay_zero(yt):
+    """The step is linear in Q: zero DOFs give exactly zero, in every precision."""
+    el, conn, Q, dt = make_case(64, 4, "unit", seed=73)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    for prec in (yt.YT_F64, yt.YT_F32, yt.YT_BF16X3_F32ACC):
+        s = yt.Solver(4, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient, precision=prec)
+        s.set_dofs_host(np.zeros_like(Q))
+        s.step()
+        s.status()
+        assert not np.any(s.get_host())
+        assert not np.any(s.get_host(yt.YT_FIELD_TIME_INTEGRAL))
+        s.close()
