@@ -8,7 +8,6 @@ import socket
 
 import numpy as np
 import pytest
-import torch
 import torch.multiprocessing as mp
 
 import workload as wl
