@@ -209,3 +209,90 @@ def test_lina_kernels_as_expressions(yt):
         ref = Q[e] + es.einsum_bruteforce('xyzp', [('z', Fh), ('xyq', out_z[e]), ('pq', Ap)]) + \
             es.einsum_bruteforce('xyzp', [('z', Fh), ('xyq', Zn[e]), ('pq', Am)])
         assert np.allclose(out[e], ref, rtol=1e-13, atol=1e-12 * np.abs(ref).max())
+
+
+def _viscoelastic_shaped(star9, n_mech, rng):
+    """27-quantity (n_mech = 3) star and source matrices with the block structure of an
+    anelastic extension: the elastic 9 x 9 block (from the elastic setup), rows of 6 memory
+    variables per mechanism driven by the three velocities (the stress-velocity pattern,
+    synthetic scale per mechanism), and a source coupling memory variables to themselves
+    (decay) and to the stresses.  Values synthetic; the paper gives no equations for this
+    rheology, so only the contraction structure is exercised."""
+    E = star9.shape[0]
+    P = 9 + 6 * n_mech
+    A = np.zeros((E, 3, P, P))
+    A[:, :, :9, :9] = star9
+    Esrc = np.zeros((E, P, P))
+    for m in range(n_mech):
+        r = 9 + 6 * m
+        A[:, :, r:r + 6, 6:9] = star9[:, :, 0:6, 6:9] * rng.uniform(0.1, 1.0, (E, 1, 1, 1))
+        w = rng.uniform(0.5, 2.0, E)
+        Esrc[:, r:r + 6, r:r + 6] = -w[:, None, None] * np.eye(6)
+        Esrc[:, 0:6, r:r + 6] = rng.uniform(-1.0, 1.0, (E, 6, 6)) * np.eye(6)
+    return A, Esrc
+
+
+@pytest.mark.parametrize("precision, tol", [(0, 1e-12), (1, 5e-6)])
+def test_viscoelastic_shaped_kernels_as_expressions(yt, precision, tol):
+    """Derivative with a reactive source term, volume and local flux of a 27-quantity
+    system, block-sparse per-element matrices passed with their patterns, order 6, against
+    the plain definition (matrix products in FP64) and, for two elements, Eq. gentensorop.
+    FP32 bound 5e-6: binary32 rounding (6e-8) over sums of up to 56 + 27 products."""
+    rng = np.random.default_rng(27)
+    order, E = 6, 40
+    N, _, star, loc, _, _ = _seissol_inputs(order, E)
+    m = basis.float_matrices(N)
+    B, P = basis.n_basis(N), 27
+    A, Esrc = _viscoelastic_shaped(star, 3, rng)
+    D = rng.standard_normal((E, B, P))
+    per = {'D': D, 'Es': Esrc, **{f"A{x}": A[:, x] for x in range(3)}}
+    consts = {f"K{x}": (m['Ktilde'][x], None) for x in range(3)}
+    expr = "D1[kp] = K0[kl]*D[lq]*A0[pq] + K1[kl]*D[lq]*A1[pq] + K2[kl]*D[lq]*A2[pq] + D[kq]*Es[pq]"
+    # per-element block patterns: the executor multiplies only their non-zeros
+    tensors_pat = {f"A{x}": (A[:, x] != 0).any(axis=0) for x in range(3)}
+    tensors_pat['Es'] = (Esrc != 0).any(axis=0)
+    out, plan = _run_with_patterns(yt, expr, consts, per, tensors_pat, 'D1', (B, P), E, precision)
+    ref = sum(np.matmul(np.matmul(m['Ktilde'][x], D), np.swapaxes(A[:, x], -1, -2)) for x in range(3)) \
+        + np.matmul(D, np.swapaxes(Esrc, -1, -2))
+    assert np.linalg.norm(out - ref) <= tol * np.linalg.norm(ref)
+    assert plan.stats()['n_terms'] == 4
+    if precision == 0:
+        for e in (0, E - 1):
+            bf = sum(es.einsum_bruteforce('kp', [('kl', m['Ktilde'][x]), ('lq', D[e]), ('pq', A[e, x])])
+                     for x in range(3)) + es.einsum_bruteforce('kp', [('kq', D[e]), ('pq', Esrc[e])])
+            assert np.allclose(out[e], bf, rtol=1e-13, atol=1e-12 * np.abs(bf).max())
+    # volume with the 27 x 27 stars
+    consts = {f"K{x}": (m['Khat'][x], None) for x in range(3)}
+    Q = rng.standard_normal((E, B, P))
+    per = {'I': D, **{f"A{x}": A[:, x] for x in range(3)}}
+    out, _ = _run_with_patterns(yt, "V[kp] += K0[kl]*I[lq]*A0[pq] + K1[kl]*I[lq]*A1[pq] + K2[kl]*I[lq]*A2[pq]",
+                                consts, per, tensors_pat, 'V', (B, P), E, precision, out_init=Q)
+    ref = Q + sum(np.matmul(np.matmul(m['Khat'][x], D), np.swapaxes(A[:, x], -1, -2)) for x in range(3))
+    assert np.linalg.norm(out - ref) <= tol * np.linalg.norm(ref)
+    # local flux of face 0 with a dense 27 x 27 flux solver
+    Al = rng.standard_normal((E, P, P))
+    consts = {'Rh': (m['Rhat'][0], None), 'R': (m['R'][0], None)}
+    out, _ = _run_with_patterns(yt, "F[kp] = Rh[km] * R[lm] * I[lq] * Al[pq]", consts,
+                                {'I': D, 'Al': Al}, {}, 'F', (B, P), E, precision)
+    ref = np.matmul(np.matmul(m['FmHat'][0], D), np.swapaxes(Al, -1, -2))
+    assert np.linalg.norm(out - ref) <= tol * np.linalg.norm(ref)
+
+
+def _run_with_patterns(yt, expr, consts, per_elem, patterns, out_name, out_shape, E, precision,
+                       out_init=None):
+    """As run(), with non-zero patterns for per-element tensors."""
+    import torch
+    dtype = np.float64 if precision == 0 else np.float32
+    tensors, dev = [], {}
+    for name, arr in per_elem.items():
+        tensors.append((name, arr.shape[1:], patterns.get(name), None))
+        dev[name] = to_dev(arr, dtype)
+    init = out_init if out_init is not None else np.full((E,) + out_shape, 7.0)
+    tensors.append((out_name, out_shape, None, None))
+    dev[out_name] = to_dev(init, dtype)
+    for name, (val, pat) in consts.items():
+        tensors.append((name, val.shape, pat, val))
+    plan = yt.Plan(expr, tensors, precision=precision)
+    plan.execute(dev, E)
+    torch.cuda.synchronize()
+    return from_dev(dev[out_name], out_shape), plan

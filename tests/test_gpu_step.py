@@ -294,3 +294,25 @@ def test_zero_dofs_stay_zero(yt):
         assert not np.any(s.get_host())
         assert not np.any(s.get_host(yt.YT_FIELD_TIME_INTEGRAL))
         s.close()
+
+
+@pytest.mark.parametrize("prec_name, order, tol", [("YT_F64", 6, 1e-12), ("YT_F32", 7, 1e-5),
+                                                   ("YT_BF16X3_F32ACC", 6, 1e-4)])
+def test_jittered_structured_mesh_steps(yt, prec_name, order, tol):
+    """Three steps on the jittered periodic structured mesh (vertices moved by up to 0.1 h,
+    the mesh family of the order-7 FP32 workload) against three oracle steps, random
+    impedance-scaled DOFs; error per quantity relative to the norm of the whole solution
+    change (stated bounds: FP64 1e-12, FP32 1e-5, split-bf16 1e-4)."""
+    N = order - 1
+    mesh = wl.jittered_periodic_mesh(3, jitter=0.1, seed=17)
+    el = mesh.elements
+    dt = wl.cfl_time_step(el, N)
+    Q0 = wl.random_dofs(el.rho.size, basis.n_basis(N), seed=18, scale="impedance", elements=el)
+    q, _ = run_gpu_prec(yt, el, mesh.conn, Q0, dt, order, getattr(yt, prec_name), steps=3)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    Q = Q0
+    for _ in range(3):
+        Q, _ = scheme.ader_step(Q, star, loc, nb, mesh.conn.neighbours, mesh.conn.faces,
+                                mesh.conn.orient, dt, N)
+    err = np.sqrt(((q - Q) ** 2).sum(axis=(0, 1))).max() / np.sqrt(((Q - Q0) ** 2).sum())
+    assert err < tol, err

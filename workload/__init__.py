@@ -170,3 +170,68 @@ def periodic_cube_mesh(n: int, length: float = 1.0, rho=1.0, lam=2.0, mu=1.0) ->
             neighbours[e, s], faces[e, s], orient[e, s] = f, t, hh
     el = Elements(np.full(E, float(rho)), np.full(E, float(lam)), np.full(E, float(mu)), jac)
     return Mesh(verts, el, Connectivity(neighbours, faces, orient), h)
+
+
+_KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+_ROTATIONS = np.array([[0, 2, 1], [1, 0, 2], [2, 1, 0]])
+
+
+def jittered_periodic_mesh(n: int, jitter: float = 0.0, seed: int = SEED + 800,
+                           length: float = 1.0, rho=1.0, lam=2.0, mu=1.0) -> Mesh:
+    """The mesh of ``periodic_cube_mesh`` built with array operations (n = 55 gives
+    998,250 tets in seconds), with every periodic vertex moved by jitter * h * U[-1, 1]^3
+    (one displacement per periodic vertex id, so that the periodic images of a vertex
+    move together and the mesh stays conforming).  jitter = 0 reproduces
+    ``periodic_cube_mesh`` element by element."""
+    if n < 3:
+        raise ValueError("n >= 3 keeps the periodic vertex ids of a face distinct")
+    h = length / n
+    g = np.arange(n)
+    corner = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 1, 3)
+    unit = np.eye(3, dtype=np.int64)
+    tets = []
+    for pm in _KUHN_PERMS:
+        p1 = unit[pm[0]]
+        p2 = p1 + unit[pm[1]]
+        order = [0, 1, 2, 3]
+        if np.linalg.det(np.stack([p1, p2, np.ones(3)], axis=1)) < 0:
+            order = [0, 2, 1, 3]
+        local = np.stack([np.zeros(3, np.int64), p1, p2, np.ones(3, np.int64)])[order]
+        tets.append(local)
+    lattice = corner[:, None] + np.stack(tets)[None]            # (n^3, 6, 4, 3)
+    lattice = lattice.reshape(-1, 4, 3)
+    E = lattice.shape[0]
+    wrapped = lattice % n
+    ids = (wrapped[..., 0] * n + wrapped[..., 1]) * n + wrapped[..., 2]    # (E, 4)
+    verts = lattice.astype(np.float64) * h
+    if jitter > 0.0:
+        disp = _rng(seed).uniform(-1.0, 1.0, (n ** 3, 3)) * (jitter * h)
+        verts = verts + disp[ids]
+    jac = np.stack([verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0],
+                    verts[:, 3] - verts[:, 0]], axis=2)
+    if not (np.linalg.det(jac) > 0).all():
+        raise ValueError("jitter too large: an element is inverted")
+    fv = np.array(FACE_VERTICES)
+    face_ids = ids[:, fv]                                       # (E, 4, 3)
+    s = np.sort(face_ids, axis=-1).reshape(-1, 3).astype(np.int64)
+    key = (s[:, 0] * n ** 3 + s[:, 1]) * n ** 3 + s[:, 2]
+    perm = np.argsort(key, kind="stable")
+    a, b = perm[0::2], perm[1::2]
+    if not (key[a] == key[b]).all() or (a.size > 1 and (key[a[1:]] == key[b[:-1]]).any()):
+        raise AssertionError("non-conforming periodic mesh")
+    slot = face_ids.reshape(-1, 3)
+    neighbours = np.empty(4 * E, np.int32)
+    faces = np.empty(4 * E, np.int8)
+    orient = np.empty(4 * E, np.int8)
+    for x, y in ((a, b), (b, a)):
+        loc, oth = slot[x], slot[y]
+        hh = np.argmax(loc == oth[:, :1], axis=1)
+        expect = np.take_along_axis(loc, _ROTATIONS[hh], axis=1)
+        if not (expect == oth).all():
+            raise AssertionError("inconsistent face orientation")
+        neighbours[x] = y // 4
+        faces[x] = y % 4
+        orient[x] = hh
+    el = Elements(np.full(E, float(rho)), np.full(E, float(lam)), np.full(E, float(mu)), jac)
+    conn = Connectivity(neighbours.reshape(E, 4), faces.reshape(E, 4), orient.reshape(E, 4))
+    return Mesh(verts, el, conn, h)
