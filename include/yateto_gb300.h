@@ -178,7 +178,7 @@ typedef struct yt_mesh_desc {
 } yt_mesh_desc;
 
 typedef struct yt_scheme_desc {
-  int32_t order;             /* convergence order O = N + 1; this build: 2..6 */
+  int32_t order;             /* convergence order O = N + 1: 2..7 */
   double dt;                 /* time step */
   yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7), YT_BF16X3_F32ACC (2..6) */
   int32_t flags;             /* reserved, must be 0 */
@@ -243,8 +243,8 @@ yt_status yt_solver_reference_matrix(const struct yt_solver* solver, const char*
 void yt_solver_destroy(struct yt_solver* solver);
 
 /* ------------------------------------------------------------- p-adaptive batches
- * Elements of different polynomial degrees in one mesh (orders 2..7 per element; order 7
- * needs YT_F32).  Each element uses its own degree for derivatives, time integral,
+ * Elements of different polynomial degrees in one mesh (orders 2..7 per element, YT_F64
+ * or YT_F32).  Each element uses its own degree for derivatives, time integral,
  * volume and local flux; across a face, the neighbour's face projection is truncated or
  * zero-padded to the element's face basis (the hierarchical orthogonal basis makes this
  * the L2 projection).  The elements are grouped by degree; one step is one launch of a
@@ -282,7 +282,7 @@ void yt_batch_destroy(struct yt_batch* batch);
  * server uses the device that is current at yt_server_create. */
 typedef struct yt_server_desc {
   int64_t hbm_budget_bytes;
-  yt_precision precision;    /* YT_F64 (orders 2..6) or YT_F32 (orders 2..7) */
+  yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7) */
   int32_t flags;             /* reserved, must be 0 */
 } yt_server_desc;
 

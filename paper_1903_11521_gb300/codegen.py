@@ -1,6 +1,6 @@
 """Build-time generator of the unrolled sparse loops of the ADER-DG kernels.
 
-For every polynomial degree N = 1..5 it emits ``_build/gen/yt_rows_o{N}.cuh`` with one
+For every polynomial degree N = 1..6 it emits ``_build/gen/yt_rows_o{N}.cuh`` with one
 specialisation ``Row<N, LIST, ROW>`` per row of every sparse list of the step (the CK
 derivative lists Ktilde^x restricted to the staircase, Khat^x, R^sT and Rhat^s): a
 straight-line sum over the row's non-zeros, values read at fixed offsets of the value
@@ -23,9 +23,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ORDERS_N = (1, 2, 3, 4, 5, 6)
-# (degree, contraction type) pairs that get kernels; degree 6 in FP64 does not fit the
-# shared memory of one CTA
-UNITS = [(n, "f64") for n in (1, 2, 3, 4, 5)] + [(n, "f32") for n in (1, 2, 3, 4, 5, 6)]
+# (degree, contraction type) pairs that get kernels
+UNITS = [(n, "f64") for n in (1, 2, 3, 4, 5, 6)] + [(n, "f32") for n in (1, 2, 3, 4, 5, 6)]
 ROW_STRIDE = 9 * 32          # doubles between consecutive rows of a thread's column
 N_ACC = 4
 

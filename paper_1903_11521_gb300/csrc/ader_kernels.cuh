@@ -188,6 +188,17 @@ template <int N, typename Real>
 struct LocalRegRows {
   static constexpr int value = (sizeof(Real) == 8 && N >= 5) ? Dims<N>::nd(1) : Dims<N>::B;
 };
+// Exchange rows of k_local.  FP64 at degree 6 (order 7) mixes the derivatives in chunks
+// of 5 rows (15 exchange rows of their own) and runs the exchange of the volume and flux
+// phases (up to max(3 KC, BT) = 28 rows) in the time-integral accumulator rows, which
+// are free once I is published: (28 + 15) operand / exchange rows + 56 accumulator rows
+// of 9 x 32 doubles = 228 KB, where separate buffers would need 258 KB.
+template <int N, typename Real>
+struct LocalExchange {
+  static constexpr bool alias = sizeof(Real) == 8 && N >= 6;
+  static constexpr int KCK = alias ? 5 : Dims<N>::KC;        // rows per derivative chunk
+  static constexpr int XR = alias ? 3 * KCK : Dims<N>::XR;   // exchange rows of their own
+};
 // Shared memory of k_local ([rows][9][32] each): operand rows not in registers, the
 // exchange buffer, and the binary64 time-integral accumulator when any operand row is
 // in registers (it is in registers otherwise).
@@ -195,8 +206,21 @@ template <int N, typename Real>
 constexpr size_t local_smem_bytes() {
   using Dm = Dims<N>;
   constexpr int RS = LocalRegRows<N, Real>::value;
-  return (size_t)sizeof(Real) * (Dm::B - RS + Dm::XR) * kNq * kTile +
+  return (size_t)sizeof(Real) * (Dm::B - RS + LocalExchange<N, Real>::XR) * kNq * kTile +
          (RS > 0 ? (size_t)8 * Dm::nd(1) * kNq * kTile : 0);
+}
+// Face slots of k_neigh's shared memory ([slot][BT][9][32]): four (the four faces lifted
+// together), or three for FP64 at degree 6, where four slots (258 KB) exceed one CTA's
+// shared memory: faces 0 and 1 are lifted after face 1, faces 2 and 3 after face 3, and
+// face 3 reuses slot 0.
+template <int N, typename Real>
+struct NeighSlots {
+  static constexpr int value = (sizeof(Real) == 8 && N >= 6) ? 3 : 4;
+  static constexpr int slot(int s) { return (value == 4 || s < 3) ? s : 0; }
+};
+template <int N, typename Real>
+constexpr size_t neigh_smem_bytes() {
+  return (size_t)sizeof(Real) * NeighSlots<N, Real>::value * Dims<N>::BT * kNq * kTile;
 }
 // Sparse row with the operand column split at RS: rows < RS in D (registers), rows >= RS
 // in shared memory at xs (that part of this thread's column, stride 9 x 32).
@@ -224,7 +248,7 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
   using Dm = Dims<N>;
   if constexpr (DELTA < N) {
     constexpr int nout = Dm::nd(DELTA + 1);
-    constexpr int KC = Dm::KC;
+    constexpr int KC = LocalExchange<N, Real>::KCK;
     constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
     const Real* xcol = Dsh + w * kTile + lane;
     const Real dtr = (Real)dt;
@@ -287,10 +311,14 @@ __global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value)
 k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
         const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
-  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC, XR = Dm::XR;
+  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
+  constexpr int XR = LocalExchange<N, Real>::XR;
+  constexpr bool ALIAS = LocalExchange<N, Real>::alias;
   constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
   constexpr int RS = LocalRegRows<N, Real>::value;   // operand rows in registers
   constexpr int SD = RS > 0 ? RS : 1;
+  static_assert(!ALIAS || (RS > 0 && sizeof(Real) == 8 && Dm::nd(1) >= Dm::XR),
+                "the volume / flux exchange must fit the accumulator rows");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // [B - RS operand rows][XR exchange rows][NI accumulator rows (double), when RS > 0]
   Real* Dsh = reinterpret_cast<Real*>(smem_raw);
@@ -362,6 +390,10 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   // local flux is then added face by face (every row of an element column belongs to
   // one thread, so these read-modify-writes need no synchronisation).
   double* Qo = Qout + tile * (kNq * B * kTile);
+  // exchange of the volume and flux phases: the accumulator rows when ALIAS (each thread
+  // has read its own accumulator column above and writes only its own column before the
+  // next barrier)
+  if constexpr (ALIAS) Xsh = reinterpret_cast<Real*>(Ish);
 
   // volume: dQ[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q]
   static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
@@ -464,9 +496,12 @@ __global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, false>::value
 k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
         StepTables<Real> T, const TileRef* __restrict__ refs) {
   using Dm = Dims<N>;
+  using Slots = NeighSlots<N, Real>;
   constexpr int B = Dm::B, BT = Dm::BT;
+  constexpr int SLOT = BT * kNq * kTile;
+  constexpr bool CVT = MinBlocks<N, Real, false>::int_cvt;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* Wsh = reinterpret_cast<Real*>(smem_raw);  // 4 faces x BT rows x 9 x 32
+  Real* Wsh = reinterpret_cast<Real*>(smem_raw);  // slots x BT rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   size_t tile = blockIdx.x;
@@ -492,7 +527,7 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
     const int g = (c >> 4) & 7, j = (c >> 2) & 3;
     const int btn = G.bt[g];
     const Real* P = static_cast<const Real*>(G.base[g]) + ((nb * 4 + j) * kNq + w) * (size_t)btn;
-    Real* dst = Wsh + s * BT * kNq * kTile + w * kTile + lane;
+    Real* dst = Wsh + Slots::slot(s) * SLOT + w * kTile + lane;
 #pragma unroll
     for (int n = 0; n < BT; ++n) {
       if (n < btn) cp_async_elem(dst + n * kNq * kTile, P + n);
@@ -500,12 +535,31 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
     }
     cp_async_commit();
   };
+  // lifting of faces F0 .. F0 + NF - 1: every row k of Q gets the sum over these faces of
+  // Rhat^s_k. W^s, summed in the contraction type (FP64: one chain), then one binary64
+  // update (each thread reads only its own columns of Wsh)
+  double* Qt = Q + tile * (kNq * B * kTile);
+  auto lift = [&](auto f0, auto nf) {
+    constexpr int F0 = decltype(f0)::value, NF = decltype(nf)::value;
+    const Real* wcol = Wsh + w * kTile + lane;
+    static_for<0, B>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      Real dq = row_dot<N, 25 + F0, k>(T.val, wcol + Slots::slot(F0) * SLOT);
+      if constexpr (NF > 1) dq = row_dot_acc<N, 26 + F0, k>(T.val, wcol + Slots::slot(F0 + 1) * SLOT, dq);
+      if constexpr (NF > 2) dq = row_dot_acc<N, 27 + F0, k>(T.val, wcol + Slots::slot(F0 + 2) * SLOT, dq);
+      if constexpr (NF > 3) dq = row_dot_acc<N, 28 + F0, k>(T.val, wcol + Slots::slot(F0 + 3) * SLOT, dq);
+      Qt[(w * B + k) * kTile + lane] += to_f64<Real, CVT>(dq);
+    });
+  };
   prefetch(std::integral_constant<int, 0>{});
   static_for<0, 4>([&](auto face) {
     constexpr int s = decltype(face)::value;
-    Real* Xsh = Wsh + s * BT * kNq * kTile;
+    Real* Xsh = Wsh + Slots::slot(s) * SLOT;
     const int h = __ldg(conn + e * 4 + s) & 3;
-    if constexpr (s < 3) {
+    // with three slots, face 3's slot (0) is free only once every thread has lifted faces
+    // 0 and 1: its copy is issued after face 2's first barrier
+    constexpr bool late = Slots::value == 3 && s == 2;
+    if constexpr (s < 3 && !late) {
       prefetch(std::integral_constant<int, s + 1>{});
       cp_async_wait<1>();
     } else {
@@ -531,6 +585,7 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
 #pragma unroll
     for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
     __syncthreads();
+    if constexpr (late) prefetch(std::integral_constant<int, 3>{});
     Real Wr[BT];
 #pragma unroll
     for (int m = 0; m < BT; ++m) {
@@ -543,20 +598,13 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < BT; ++m) Xsh[(m * kNq + w) * kTile + lane] = Wr[m];
+    if constexpr (Slots::value == 3 && s == 1) lift(std::integral_constant<int, 0>{}, std::integral_constant<int, 2>{});
   });
   // every thread reads only its own columns of Wsh below: no barrier needed
-  double* Qt = Q + tile * (kNq * B * kTile);
-  static_for<0, B>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    const Real* wcol = Wsh + w * kTile + lane;
-    // the four faces' lifted rows summed in the contraction type (FP64: one chain), then
-    // one binary64 update
-    Real dq = row_dot<N, 25, k>(T.val, wcol);
-    dq = row_dot_acc<N, 26, k>(T.val, wcol + 1 * BT * kNq * kTile, dq);
-    dq = row_dot_acc<N, 27, k>(T.val, wcol + 2 * BT * kNq * kTile, dq);
-    dq = row_dot_acc<N, 28, k>(T.val, wcol + 3 * BT * kNq * kTile, dq);
-    Qt[(w * B + k) * kTile + lane] += to_f64<Real, MinBlocks<N, Real, false>::int_cvt>(dq);
-  });
+  if constexpr (Slots::value == 4)
+    lift(std::integral_constant<int, 0>{}, std::integral_constant<int, 4>{});
+  else
+    lift(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -608,6 +656,10 @@ inline size_t ader_local_smem(int N, bool f32) {
   }
   return 0;
 }
+inline size_t ader_neigh_smem(int N, bool f32) {
+  if (N == 6) return f32 ? neigh_smem_bytes<6, float>() : neigh_smem_bytes<6, double>();
+  return (f32 ? 4 : 8) * (size_t)(4 * ((N + 1) * (N + 2) / 2)) * kNq * kTile;
+}
 
 // Launch functions of one kernel variant (LOCAL: k_local<N, !FUSED>; else
 // k_neigh<N, FUSED>); the generated translation units instantiate one variant each.
@@ -635,8 +687,7 @@ void ader_launch(const AderLaunch& L) {
 
 // Per-degree, per-precision, per-variant instantiations live in generated translation
 // units (ader_o<N>_<f64|f32>_<variant>.cu, variant = lf: local fused, ll: local lifted,
-// nf: neighbour fused, np: neighbour plain).  Degree 6 exists in f32 only: its FP64
-// shared-memory footprint (258 KB) exceeds the 227 KB a CTA may use.
+// nf: neighbour fused, np: neighbour plain).
 #define YT_DECLARE_ADER_VARIANT(N, P, V)                  \
   void ader_set_attribute_o##N##_##P##_##V(size_t);      \
   void ader_launch_o##N##_##P##_##V(const AderLaunch&);  \
@@ -651,6 +702,7 @@ YT_DECLARE_ADER_UNIT(2, f64)
 YT_DECLARE_ADER_UNIT(3, f64)
 YT_DECLARE_ADER_UNIT(4, f64)
 YT_DECLARE_ADER_UNIT(5, f64)
+YT_DECLARE_ADER_UNIT(6, f64)
 YT_DECLARE_ADER_UNIT(1, f32)
 YT_DECLARE_ADER_UNIT(2, f32)
 YT_DECLARE_ADER_UNIT(3, f32)

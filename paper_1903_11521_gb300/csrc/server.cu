@@ -301,7 +301,7 @@ extern "C" yt_status yt_server_submit(yt_server* sv, const yt_mesh_desc* mesh, i
     YT_REQUIRE(sv && mesh && dofs && request_id, YT_ERR_INVALID, "null argument");
     YT_REQUIRE(mesh->n_elements > 1 && mesh->material && mesh->jacobian && mesh->neighbours &&
                    mesh->faces && mesh->orient, YT_ERR_INVALID, "mesh needs full connectivity");
-    YT_REQUIRE(order >= 2 && order <= (sv->prec == YT_F32 ? 7 : 6), YT_ERR_UNSUPPORTED, "order");
+    YT_REQUIRE(order >= 2 && order <= 7, YT_ERR_UNSUPPORTED, "order");
     YT_REQUIRE(n_steps > 0, YT_ERR_INVALID, "n_steps must be positive");
     YT_REQUIRE(dt > 0, YT_ERR_INVALID, "dt must be positive");
     auto r = std::make_unique<Request>();

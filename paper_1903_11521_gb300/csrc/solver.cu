@@ -230,6 +230,7 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
       case 9: FN##_o4_f32_##V(__VA_ARGS__); break;                            \
       case 10: FN##_o5_f64_##V(__VA_ARGS__); break;                           \
       case 11: FN##_o5_f32_##V(__VA_ARGS__); break;                           \
+      case 12: FN##_o6_f64_##V(__VA_ARGS__); break;                           \
       case 13: FN##_o6_f32_##V(__VA_ARGS__); break;                           \
       default: throw Error(YT_ERR_UNSUPPORTED, "no kernel for this order and precision"); \
     }                                                                          \
@@ -252,9 +253,8 @@ void set_smem(yt_solver* s) {
     cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
     return;
   }
-  const int BT = n_face_basis(N);
   s->smem_local = ader_local_smem(N, s->prec != YT_F64);
-  s->smem_neigh = s->real_bytes * (size_t)(4 * BT) * kNq * kTile;
+  s->smem_neigh = ader_neigh_smem(N, s->prec != YT_F64);
   YT_REQUIRE(s->smem_local <= 227 * 1024 && s->smem_neigh <= 227 * 1024, YT_ERR_UNSUPPORTED,
              "order too high for this precision");
   YT_VARIANT_SWITCH(ader_set_attribute, lf, s->smem_local);
@@ -473,8 +473,8 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32 ||
                    scheme->precision == YT_BF16X3_F32ACC,
                YT_ERR_UNSUPPORTED, "solver precision: YT_F64, YT_F32 or YT_BF16X3_F32ACC");
-    YT_REQUIRE(scheme->precision == YT_F32 || scheme->order <= 6, YT_ERR_UNSUPPORTED,
-               "YT_F64 and YT_BF16X3_F32ACC solvers: orders 2..6 (order 7 needs YT_F32)");
+    YT_REQUIRE(scheme->precision != YT_BF16X3_F32ACC || scheme->order <= 6, YT_ERR_UNSUPPORTED,
+               "YT_BF16X3_F32ACC solvers: orders 2..6");
     YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
     YT_REQUIRE(mesh->n_elements < (int64_t(1) << 24), YT_ERR_UNSUPPORTED, "at most 2^24 elements");
     const bool nb = mesh->neighbours != nullptr;

@@ -65,6 +65,17 @@ def test_mixed_orders_fp64(yt):
     assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 1e-11
 
 
+def test_mixed_orders_fp64_up_to_order7(yt):
+    el, conn, orders, Q, dt = case(120, 3, 7, 61)
+    q, i, _, st = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F64)
+    star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
+    ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
+                                    conn.orient, dt)
+    assert st['groups'] == 5
+    assert per_quantity(i, I).max() < 1e-12
+    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 1e-11
+
+
 def test_mixed_orders_fp32_up_to_order7(yt):
     el, conn, orders, Q, dt = case(120, 3, 7, 60)
     q, i, _, _ = batch_run(yt, el, conn, orders, Q, dt, yt.YT_F32)

@@ -48,7 +48,7 @@ def run_gpu(yt, el, conn, Q, dt, order, full=True):
     return q, i
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("E", [1, 37, 100])
 def test_local_step_parity(yt, order, E):
     """K_local alone (derivatives, time integral, volume, local flux) — the O4 / 1000-tet
@@ -65,7 +65,7 @@ def test_local_step_parity(yt, order, E):
     assert rel_per_quantity(q_gpu - Q, q_ref - Q).max() < 1e-11
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
 def test_full_step_parity(yt, order):
     E = 70
     el, conn, Q, dt = make_case(E, order, "impedance", seed=7)
@@ -296,8 +296,8 @@ def test_zero_dofs_stay_zero(yt):
         s.close()
 
 
-@pytest.mark.parametrize("prec_name, order, tol", [("YT_F64", 6, 1e-12), ("YT_F32", 7, 1e-5),
-                                                   ("YT_BF16X3_F32ACC", 6, 1e-4)])
+@pytest.mark.parametrize("prec_name, order, tol", [("YT_F64", 6, 1e-12), ("YT_F64", 7, 1e-12),
+                                                   ("YT_F32", 7, 1e-5), ("YT_BF16X3_F32ACC", 6, 1e-4)])
 def test_jittered_structured_mesh_steps(yt, prec_name, order, tol):
     """Three steps on the jittered periodic structured mesh (vertices moved by up to 0.1 h,
     the mesh family of the order-7 FP32 workload) against three oracle steps, random
