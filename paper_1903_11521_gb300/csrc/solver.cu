@@ -341,43 +341,62 @@ void build_tables(yt_solver* s) {
   const int N = s->N, B = R.B, BT = R.BT;
   Csr csr;
   auto nd = [N](int delta) { return (N - delta + 3) * (N - delta + 2) * (N - delta + 1) / 6; };
+  // Non-zero flops per element in the convention of Sec. 4.9: an entry that is a sum of n
+  // non-zero products costs 2n - 1 flops when assigned and 2n when added to an existing
+  // value; a scaling costs 1.  The derivatives' factor dt (an implementation choice that
+  // keeps their magnitude bounded) is not counted.
+  auto assigned = [&](int off, int rows) {
+    double f = 0.0;
+    for (int r = 0; r < rows; ++r) {
+      const int n = csr.row_nnz(off, r);
+      if (n > 0) f += 9.0 * (2.0 * n - 1.0);
+    }
+    return f;
+  };
+  auto nnz_total = [&](int off, int rows) {
+    double n = 0.0;
+    for (int r = 0; r < rows; ++r) n += csr.row_nnz(off, r);
+    return n;
+  };
+  // mixing with the three star matrices: entry p sums 3 * cnt_p products (cnt_p = non-zeros
+  // of star row p, 24 per matrix): assigned sum_p (6 cnt_p - 1) = 135, added 144 per row
+  const double mix_assigned = 6.0 * kStarSlots - 9.0, mix_added = 6.0 * kStarSlots;
   double fl = 9.0 * B;                                     // I = c0 Q
   for (int delta = 0; delta < N; ++delta) {
     const int nin = nd(delta), nout = nd(delta + 1);
     for (int x = 0; x < 3; ++x) {
       const double* K = R.Ktilde.data() + (size_t)x * B * B;
       const int off = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; });
-      for (int r = 0; r < nout; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off, r) + 1.0);
+      fl += assigned(off, nout);                           // X^x = Ktilde^x D
     }
-    fl += nout * (2.0 * 3 * kStarSlots + 9.0 + 2.0 * 9);  // mixing, dt scaling, time integral
+    fl += nout * (mix_assigned + 2.0 * 9);                 // D' = sum_x X^x A^xT; I += c D'
   }
   for (int x = 0; x < 3; ++x) {
     const double* K = R.Khat.data() + (size_t)x * B * B;
     const int off = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
-    for (int r = 0; r < B; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off, r) + 1.0);
+    fl += assigned(off, B);                                // X^x = Khat^x I
   }
-  fl += B * 2.0 * 3 * kStarSlots;
+  fl += B * mix_added;                                     // Q += sum_x X^x A^xT
   double fn = 0.0, lift_total = 0.0;
   for (int f = 0; f < 4; ++f) {
     const double* Rs = R.R.data() + (size_t)f * B * BT;
     const double* Rh = R.Rhat.data() + (size_t)f * B * BT;
     const int off_rt = csr.add(BT, B, [&](int r, int c) { return Rs[c + (size_t)r * B]; });
     const int off_rh = csr.add(B, BT, [&](int r, int c) { return Rh[r + (size_t)c * B]; });
-    double lift = 0.0;
-    for (int r = 0; r < BT; ++r) fl += 9.0 * (2.0 * csr.row_nnz(off_rt, r) + 1.0);
-    for (int r = 0; r < B; ++r) lift += 9.0 * (2.0 * csr.row_nnz(off_rh, r) + 1.0 + 1.0);
-    fl += BT * 2.0 * 81;
+    fl += assigned(off_rt, BT);                            // P = R^T I
+    fl += BT * 9.0 * 17.0;                                 // Wloc = P Aloc^T
+    const double lift = 9.0 * 2.0 * nnz_total(off_rh, B);  // Q += Rhat W (per face)
     lift_total += lift;
-    double blocks = 0.0;
-    for (int d = 0; d <= N; ++d) blocks += (d + 1.0) * (d + 1.0);
-    fn += 9.0 * 2.0 * blocks + BT * 2.0 * 81 + lift;
+    double blocks = 0.0;                                   // V = f^h P_nb, block-diagonal
+    for (int d = 0; d <= N; ++d) blocks += (d + 1.0) * (2.0 * (d + 1.0) - 1.0);
+    fn += 9.0 * blocks + BT * 9.0 * 18.0 + lift;           // W = Wloc + V Anb^T; lifting
   }
-  fl += 9.0 * B;                                           // Q + dQ
-  fn += 9.0 * B;
-  // yt_step runs k_local without the local lifting and k_neigh with the local products
-  // added (one addition per entry of W) before the single lifting
+  // yt_step runs k_local without the local lifting and k_neigh with the sum of both flux
+  // products lifted once (the flops of the lifting are the same as lifting them one by
+  // one: every non-zero product is added to Q); the unfused pair lifts the local products
+  // in k_local and computes W = V Anb^T (17 per entry) in k_neigh
   s->flops_local = fl;
-  s->flops_neigh = fn + 4.0 * 9 * BT;
+  s->flops_neigh = fn;
   s->flops_local_unfused = fl + lift_total;
   const double rb = (double)s->real_bytes;
   const double qb = 8.0 * 9 * B, pb = rb * 4 * 9 * BT;

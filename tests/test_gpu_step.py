@@ -316,3 +316,49 @@ def test_jittered_structured_mesh_steps(yt, prec_name, order, tol):
                                 mesh.conn.orient, dt, N)
     err = np.sqrt(((q - Q) ** 2).sum(axis=(0, 1))).max() / np.sqrt(((Q - Q0) ** 2).sum())
     assert err < tol, err
+
+
+def _nonzero_flops(order):
+    """Non-zero flops per element of the two step kernels in the convention of Sec. 4.9
+    (a sum of n products: 2n - 1 flops assigned, 2n added to an existing value; a scaling:
+    1), counted here from the oracle's matrices: derivatives restricted to the staircase,
+    volume, face projections, 9 x 9 mixing with the 24-non-zero star matrices, flux
+    solvers, block-diagonal f^h, lifting of both flux terms."""
+    N = order - 1
+    m = basis.float_matrices(N)
+    B, BT = basis.n_basis(N), basis.n_face_basis(N)
+    nd = lambda d: (N - d + 3) * (N - d + 2) * (N - d + 1) // 6   # noqa: E731
+    star_nnz = 24
+
+    def assigned(M):
+        n = (M != 0).sum(axis=1)
+        return 9 * int(np.where(n > 0, 2 * n - 1, 0).sum())
+
+    local = 9 * B
+    for d in range(N):
+        for x in range(3):
+            local += assigned(m['Ktilde'][x][:nd(d + 1), :nd(d)])
+        local += nd(d + 1) * ((6 * star_nnz - 9) + 2 * 9)
+    for x in range(3):
+        local += assigned(m['Khat'][x])
+    local += B * 6 * star_nnz
+    neigh = 0
+    for s in range(4):
+        local += assigned(m['R'][s].T) + BT * 9 * 17
+        blocks = sum((d + 1) * (2 * (d + 1) - 1) for d in range(N + 1))
+        neigh += 9 * blocks + BT * 9 * 18 + 9 * 2 * int((m['Rhat'][s] != 0).sum())
+    return local, neigh
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+def test_flop_counts_match_pattern_count(yt, order):
+    """The flops the library reports (used for every roofline fraction) equal an
+    independent count from the oracle's sparsity patterns."""
+    el, conn, Q, dt = make_case(40, order, "unit")
+    s = yt.Solver(order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac, conn.neighbours,
+                  conn.faces, conn.orient)
+    st = s.stats()
+    s.close()
+    local, neigh = _nonzero_flops(order)
+    assert st['local_flops'] == local
+    assert st['neighbour_flops'] == neigh
