@@ -148,13 +148,15 @@ def test_phases_equal_step_and_unfused_path(yt):
     assert rel_per_quantity(outs[2], outs[0]).max() < TOL
 
 
+@pytest.mark.parametrize("E", [8 * 32 * 3 + 45, 512 * 32 + 77])
 @pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32", "YT_BF16X3_F32ACC"])
-def test_step_host_equals_step(yt, prec_name):
-    """yt_step_host (pipelined copies, 8 element chunks, ragged last chunk) gives bitwise
-    the result of set_dofs + yt_step + get on the same solver; also in place."""
+def test_step_host_equals_step(yt, prec_name, E):
+    """yt_step_host (pipelined copies, 8 element chunks, ragged last chunk and tile; 26 and
+    515 tiles) gives bitwise the result of set_dofs + yt_step + get on the same solver;
+    also in place."""
     import torch
     prec = getattr(yt, prec_name)
-    E, order = 8 * 32 * 3 + 45, 4
+    order = 4
     el, conn, Q, dt = make_case(E, order, "impedance", seed=61)
     mat = np.stack([el.rho, el.lam, el.mu], axis=1)
     canon = np.ascontiguousarray(Q.transpose(0, 2, 1))
