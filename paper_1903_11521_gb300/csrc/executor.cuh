@@ -92,4 +92,65 @@ k_execute(const ExecOp* __restrict__ ops, int nops, const int* __restrict__ prog
   }
 }
 
+// Element-per-warp variant: a warp takes one element at a time (grid-stride over the
+// elements), its lanes share out the output entries (rows) of each operation, and the
+// temporaries live in the warp's slice of shared memory ([warp][temp_entries]).  The
+// element's own tensors are contiguous in global memory, so the gathers of one warp stay
+// in L1.  Lanes exchange temporaries between operations, hence a __syncwarp after each.
+template <typename Real>
+__device__ __forceinline__ Real ew_load(int kind, int ref, int off, const Real* __restrict__ consts,
+                                        const ExecPtrs<Real>& T, const Real* tmp, int64_t base) {
+  if (kind == kOpTemp) return tmp[ref + off];
+  if (kind == kOpConst) return __ldg(consts + ref + off);
+  if (kind == kOpTensor) return T.p[ref][base + off];
+  return Real(1);
+}
+
+// grid: any number of blocks of kEwWarps warps; dynamic shared memory kEwWarps *
+// temp_entries * sizeof(Real).
+constexpr int kEwWarps = 4;
+template <typename Real>
+__global__ void __launch_bounds__(kEwWarps * 32)
+k_execute_ew(const ExecOp* __restrict__ ops, int nops, const int* __restrict__ prog,
+             const Real* __restrict__ consts, ExecPtrs<Real> T, int temp_entries, int64_t n_elements) {
+  extern __shared__ __align__(16) unsigned char ew_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  Real* tmp = reinterpret_cast<Real*>(ew_smem) + (size_t)wib * temp_entries;
+  const int64_t n_warps = (int64_t)gridDim.x * kEwWarps;
+  for (int64_t e = (int64_t)blockIdx.x * kEwWarps + wib; e < n_elements; e += n_warps) {
+    for (int o = 0; o < nops; ++o) {
+      const ExecOp op = ops[o];
+      if (op.kind == kOpZero) {
+        Real* dst = T.p[op.out_ref] + e * op.out_size;
+        for (int i = lane; i < op.out_size; i += 32) dst[i] = Real(0);
+        __syncwarp();
+        continue;
+      }
+      const int64_t abase = e * op.a_size, bbase = e * op.b_size;
+      for (int r = lane; r < op.nrows; r += 32) {
+        const int oc = __ldg(prog + op.rows_off + r);
+        const int b = __ldg(prog + op.rp_off + r), en = __ldg(prog + op.rp_off + r + 1);
+        Real acc = Real(0);
+#pragma unroll 4
+        for (int t = b; t < en; ++t) {
+          const int oa = __ldg(prog + op.pairs_off + 2 * t);
+          const int ob = __ldg(prog + op.pairs_off + 2 * t + 1);
+          const Real va = ew_load<Real>(op.a_kind, op.a_ref, oa, consts, T, tmp, abase);
+          const Real vb = ew_load<Real>(op.b_kind, op.b_ref, ob, consts, T, tmp, bbase);
+          acc = fma(va, vb, acc);
+        }
+        if (op.scalar != 1.0) acc *= (Real)op.scalar;
+        if (op.out_kind == kOpTemp) {
+          tmp[op.out_ref + oc] = acc;
+        } else {
+          Real* dst = T.p[op.out_ref] + e * op.out_size + oc;
+          *dst = op.accumulate ? *dst + acc : acc;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace yt

@@ -259,10 +259,28 @@ void launch(yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t st) {
       YT_REQUIRE(ptrs[i] != nullptr, YT_ERR_INVALID, "null pointer for per-element tensor " + p->tensors[i].name);
       T.p[p->slot_of_tensor[i]] = static_cast<Real*>(ptrs[i]);
     }
-  const int64_t tiles = (n + 31) / 32;
   int dev = 0, sms = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  // one element per warp with the temporaries in shared memory when they fit in 96 KB per
+  // block of four warps (two blocks per SM at least; with one block per SM the
+  // lane-per-element kernel below was measured faster)
+  const size_t ew_smem = (size_t)kEwWarps * p->temp_entries * sizeof(Real);
+  if (ew_smem <= 96 * 1024) {
+    std::lock_guard<std::mutex> lock(p->mu);
+    ensure_device<Real>(p);
+    if (ew_smem > 48 * 1024)
+      cuda_check(cudaFuncSetAttribute(k_execute_ew<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ew_smem), "cudaFuncSetAttribute");
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + kEwWarps - 1) / kEwWarps,
+                                                                  (int64_t)sms * 16));
+    k_execute_ew<Real><<<(unsigned)blocks, kEwWarps * 32, ew_smem, st>>>(
+        p->d_ops, (int)p->ops.size(), p->d_prog, static_cast<const Real*>(p->d_consts), T,
+        p->temp_entries, n);
+    cuda_check(cudaGetLastError(), "k_execute_ew launch");
+    return;
+  }
+  const int64_t tiles = (n + 31) / 32;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, (int64_t)sms * 8));
   const size_t need = (size_t)blocks * 4 * p->temp_entries * 32 * sizeof(Real);
   std::lock_guard<std::mutex> lock(p->mu);
