@@ -296,3 +296,25 @@ def _run_with_patterns(yt, expr, consts, per_elem, patterns, out_name, out_shape
     plan.execute(dev, E)
     torch.cuda.synchronize()
     return from_dev(dev[out_name], out_shape), plan
+
+
+@pytest.mark.parametrize("S", [2, 8])
+def test_fused_simulation_chain_both_executor_kernels(yt, S):
+    """The neighbour-flux chain of one face with S fused simulations at order 6, against
+    the plain definition (matrix products): with 2 simulations the temporaries of four
+    warps fit in 96 KB of shared memory (element-per-warp kernel), with 8 they do not
+    (lane-per-element kernel, temporaries in global scratch)."""
+    rng = np.random.default_rng(40 + S)
+    order, E = 6, 37
+    N = order - 1
+    m = basis.float_matrices(N)
+    B, Bt = basis.n_basis(N), basis.n_face_basis(N)
+    J = rng.standard_normal((E, B, 9, S))
+    A = rng.standard_normal((E, 9, 9))
+    consts = {'Rh': (m['Rhat'][1], m['Rhat'][1] != 0), 'f': (m['f'][2], m['f'][2] != 0),
+              'R': (m['R'][3], m['R'][3] != 0)}
+    out, plan = run(yt, "G[kps] = Rh[km] * f[mn] * R[ln] * J[lqs] * An[pq]", consts,
+                    {'J': J, 'An': A}, 'G', (B, 9, S), E)
+    F = m['Rhat'][1] @ m['f'][2] @ m['R'][3].T
+    ref = np.einsum('kl,elqs,epq->ekps', F, J, A)
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
