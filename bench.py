@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16x3"],
                     help="contraction type of the main measurement (default FP64)")
+    ap.add_argument("--form", default=None,
+                    choices=["executor", "structured", "serving", "local_update"],
+                    help="run only this form of the forms section and print it as one JSON line "
+                         "(for profiling one form)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batching and serving measurements")
     return ap.parse_args()
@@ -549,6 +553,15 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     torch.cuda.set_device(local)
     import paper_1903_11521_gb300 as yt
+
+    if args.form:
+        stream = torch.cuda.current_stream()
+        run = {"executor": lambda: form_executor(yt, stream),
+               "structured": lambda: form_structured(yt, stream),
+               "serving": lambda: form_serving(yt),
+               "local_update": lambda: form_local_update(yt, 4, 1000, 200, stream)}[args.form]
+        print(json.dumps({"form": args.form, "result": run()}), flush=True)
+        return
 
     N = args.order - 1
     B = args.order * (args.order + 1) * (args.order + 2) // 6
