@@ -26,6 +26,7 @@ struct yt_plan {
   std::vector<int> prog;
   std::vector<int> slot_of_tensor;     // per-element tensor index -> pointer slot
   int temp_entries = 1;
+  bool element_per_warp = false;       // executor kernel, chosen at creation
   double nz_flops = 0, hw_flops = 0, naive_flops = 0;
   int64_t bytes_per_element = 0;
   int n_binary = 0;
@@ -207,6 +208,36 @@ void compile(yt_plan* p) {
     p->order += tp.order;
   }
   p->temp_entries = max_temp;
+  // kernel choice: one element per warp when four warps' temporaries fit in 96 KB of
+  // shared memory (two blocks per SM at least; with one block per SM the lane-per-element
+  // kernel was measured faster); its rows are then reordered by decreasing number of
+  // products (output entry order among equals), so that the lanes of a warp, which take
+  // consecutive rows, run similar numbers of products.  The lane-per-element kernel keeps
+  // the output entry order (its temporaries are written in that order).
+  const size_t word_bytes = p->prec == YT_F32 ? 4 : 8;
+  p->element_per_warp = (size_t)kEwWarps * p->temp_entries * word_bytes <= 96 * 1024;
+  if (p->element_per_warp) {
+    for (const ExecOp& op : p->ops) {
+      if (op.kind == kOpZero || op.nrows == 0) continue;
+      std::vector<int> idx(op.nrows);
+      for (int r = 0; r < op.nrows; ++r) idx[r] = r;
+      auto len = [&](int r) { return p->prog[op.rp_off + r + 1] - p->prog[op.rp_off + r]; };
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return len(a) > len(b); });
+      std::vector<int> rows_new, rp_new(1, 0), pairs_new;
+      for (int r : idx) {
+        rows_new.push_back(p->prog[op.rows_off + r]);
+        const int b = p->prog[op.rp_off + r], e = p->prog[op.rp_off + r + 1];
+        for (int t = b; t < e; ++t) {
+          pairs_new.push_back(p->prog[op.pairs_off + 2 * t]);
+          pairs_new.push_back(p->prog[op.pairs_off + 2 * t + 1]);
+        }
+        rp_new.push_back((int)pairs_new.size() / 2);
+      }
+      std::copy(rows_new.begin(), rows_new.end(), p->prog.begin() + op.rows_off);
+      std::copy(rp_new.begin(), rp_new.end(), p->prog.begin() + op.rp_off);
+      std::copy(pairs_new.begin(), pairs_new.end(), p->prog.begin() + op.pairs_off);
+    }
+  }
   // bytes per element: per-element operands read once, result written (and read for +=)
   std::vector<bool> seen(p->tensors.size(), false);
   const size_t word = p->prec == YT_F32 ? 4 : 8;
@@ -262,11 +293,9 @@ void launch(yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t st) {
   int dev = 0, sms = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-  // one element per warp with the temporaries in shared memory when they fit in 96 KB per
-  // block of four warps (two blocks per SM at least; with one block per SM the
-  // lane-per-element kernel below was measured faster)
+  // one element per warp with the temporaries in shared memory (kernel chosen at creation)
   const size_t ew_smem = (size_t)kEwWarps * p->temp_entries * sizeof(Real);
-  if (ew_smem <= 96 * 1024) {
+  if (p->element_per_warp) {
     std::lock_guard<std::mutex> lock(p->mu);
     ensure_device<Real>(p);
     if (ew_smem > 48 * 1024)
