@@ -109,6 +109,9 @@ __device__ __forceinline__ Real ew_load(int kind, int ref, int off, const Real* 
 // grid: any number of blocks of kEwWarps warps; dynamic shared memory kEwWarps *
 // temp_entries * sizeof(Real).
 constexpr int kEwWarps = 4;
+// plans whose four warps' temporaries fit this much shared memory use k_execute_ew (two
+// blocks per SM at least)
+constexpr int kEwSmemCap = 96 * 1024;
 template <typename Real>
 __global__ void __launch_bounds__(kEwWarps * 32)
 k_execute_ew(const ExecOp* __restrict__ ops, int nops, const int* __restrict__ prog,

@@ -215,7 +215,7 @@ void compile(yt_plan* p) {
   // consecutive rows, run similar numbers of products.  The lane-per-element kernel keeps
   // the output entry order (its temporaries are written in that order).
   const size_t word_bytes = p->prec == YT_F32 ? 4 : 8;
-  p->element_per_warp = (size_t)kEwWarps * p->temp_entries * word_bytes <= 96 * 1024;
+  p->element_per_warp = (size_t)kEwWarps * p->temp_entries * word_bytes <= (size_t)kEwSmemCap;
   if (p->element_per_warp) {
     for (const ExecOp& op : p->ops) {
       if (op.kind == kOpZero || op.nrows == 0) continue;
@@ -298,9 +298,11 @@ void launch(yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t st) {
   if (p->element_per_warp) {
     std::lock_guard<std::mutex> lock(p->mu);
     ensure_device<Real>(p);
+    // the attribute belongs to the function, shared by all plans: always the cap, so that
+    // plans launching from other threads never see a smaller value
     if (ew_smem > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_execute_ew<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)ew_smem), "cudaFuncSetAttribute");
+                                      kEwSmemCap), "cudaFuncSetAttribute");
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + kEwWarps - 1) / kEwWarps,
                                                                   (int64_t)sms * 16));
     k_execute_ew<Real><<<(unsigned)blocks, kEwWarps * 32, ew_smem, st>>>(

@@ -298,12 +298,13 @@ def _run_with_patterns(yt, expr, consts, per_elem, patterns, out_name, out_shape
     return from_dev(dev[out_name], out_shape), plan
 
 
-@pytest.mark.parametrize("S", [2, 8])
+@pytest.mark.parametrize("S", [2, 4, 8])
 def test_fused_simulation_chain_both_executor_kernels(yt, S):
     """The neighbour-flux chain of one face with S fused simulations at order 6, against
-    the plain definition (matrix products): with 2 simulations the temporaries of four
-    warps fit in 96 KB of shared memory (element-per-warp kernel), with 8 they do not
-    (lane-per-element kernel, temporaries in global scratch)."""
+    the plain definition (matrix products): with 2 and 4 simulations the temporaries of
+    four warps fit in 96 KB of shared memory (element-per-warp kernel; 4: above the 48 KB
+    that need the opt-in attribute), with 8 they do not (lane-per-element kernel,
+    temporaries in global scratch)."""
     rng = np.random.default_rng(40 + S)
     order, E = 6, 37
     N = order - 1
