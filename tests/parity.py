@@ -1,0 +1,81 @@
+"""Error measures shared by the GPU parity tests.
+
+The paper compares an optimised kernel with the naive one through the Frobenius norm of
+the difference (Sec. 4.9) without giving a value; the tests state theirs.  Two views of
+the same difference are checked:
+
+* per quantity: for every quantity p, ||X_gpu[:, :, p] - X_ref[:, :, p]||_F divided by
+  ||X_ref[:, :, p]||_F, over all elements and basis functions (a quantity with a small
+  norm keeps its own scale);
+* per element: for every element e, ||X_gpu[e] - X_ref[e]||_F / ||X_ref[e]||_F, and the
+  maximum over e.  An error confined to one element is diluted by about sqrt(E) in the
+  first view; the second one sees it at full size.
+
+Arrays are (elements, basis functions, quantities) or lists of (basis, quantities)
+arrays of different sizes (p-adaptive meshes).  `check` prints one `PARITY` line per call
+(name, both maxima, both bounds) so that a run with `-s` records the measured errors.
+"""
+import numpy as np
+
+
+def _stack(x):
+    if isinstance(x, (list, tuple)):
+        return x
+    return np.asarray(x)
+
+
+def per_quantity(got, ref):
+    if isinstance(ref, (list, tuple)):
+        g = np.concatenate([np.asarray(a) for a in got], axis=0)
+        r = np.concatenate([np.asarray(a) for a in ref], axis=0)
+        num = np.sqrt(((g - r) ** 2).sum(axis=0))
+        den = np.sqrt((r ** 2).sum(axis=0))
+    else:
+        num = np.sqrt(((got - ref) ** 2).sum(axis=(0, 1)))
+        den = np.sqrt((ref ** 2).sum(axis=(0, 1)))
+    return num / np.where(den > 0, den, 1.0)
+
+
+def per_element(got, ref):
+    if isinstance(ref, (list, tuple)):
+        num = np.array([np.linalg.norm(np.asarray(a) - np.asarray(b)) for a, b in zip(got, ref)])
+        den = np.array([np.linalg.norm(b) for b in ref])
+    else:
+        num = np.sqrt(((got - ref) ** 2).sum(axis=(1, 2)))
+        den = np.sqrt((ref ** 2).sum(axis=(1, 2)))
+    return num / np.where(den > 0, den, 1.0)
+
+
+def increment(x, base):
+    if isinstance(x, (list, tuple)):
+        return [np.asarray(a) - np.asarray(b) for a, b in zip(x, base)]
+    return x - base
+
+
+def check(name, got, ref, tol_quantity, tol_element, base=None):
+    """Asserts both views of got - ref within their bounds; with `base`, the increments
+    got - base and ref - base are compared instead (the part of Q a step changes)."""
+    got, ref = _stack(got), _stack(ref)
+    if base is not None:
+        got, ref = increment(got, base), increment(ref, base)
+    eq = float(per_quantity(got, ref).max())
+    ee = float(per_element(got, ref).max())
+    print(f"PARITY {name}: per-quantity {eq:.3e} (bound {tol_quantity:.1e}), "
+          f"per-element {ee:.3e} (bound {tol_element:.1e})")
+    assert eq < tol_quantity, (name, "per quantity", eq, tol_quantity)
+    assert ee < tol_element, (name, "per element", ee, tol_element)
+    return eq, ee
+
+
+# ------------------------------------------------------------------------- bounds
+# FP64: 1e-12 on Q and on I, 1e-11 on the increment Q_new - Q (the
+# increment is about 1e-1 of Q, so its relative error is about ten times that of Q).
+F64 = 1e-12
+F64_INC = 1e-11
+# Reduced precisions (calibration values; set from the measured maxima below).
+F32_I = 2e-6
+F32_INC = 2e-5
+TC_I = 2e-4
+TC_INC = 1e-3
+# per-element maxima sit above the per-quantity ones (the worst of E elements)
+ELEMENT_FACTOR = 10.0

@@ -3,6 +3,7 @@ oracle's mixed-order step."""
 import numpy as np
 import pytest
 
+import parity
 import workload as wl
 from oracle import basis, scheme
 
@@ -61,8 +62,8 @@ def test_mixed_orders_fp64(yt):
     ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
                                     conn.orient, dt)
     assert st['groups'] == 5
-    assert per_quantity(i, I).max() < 1e-12
-    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 1e-11
+    parity.check(f"batch f64 o{orders.min()}-{orders.max()} I", i, I, parity.F64, parity.F64)
+    parity.check(f"batch f64 o{orders.min()}-{orders.max()} dQ", q, ref, parity.F64_INC, parity.F64_INC, base=Q)
 
 
 def test_mixed_orders_fp64_up_to_order7(yt):
@@ -72,8 +73,8 @@ def test_mixed_orders_fp64_up_to_order7(yt):
     ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
                                     conn.orient, dt)
     assert st['groups'] == 5
-    assert per_quantity(i, I).max() < 1e-12
-    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 1e-11
+    parity.check(f"batch f64 o{orders.min()}-{orders.max()} I", i, I, parity.F64, parity.F64)
+    parity.check(f"batch f64 o{orders.min()}-{orders.max()} dQ", q, ref, parity.F64_INC, parity.F64_INC, base=Q)
 
 
 def test_mixed_orders_fp32_up_to_order7(yt):
@@ -82,7 +83,8 @@ def test_mixed_orders_fp32_up_to_order7(yt):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
                                     conn.orient, dt)
-    assert per_quantity([a - b for a, b in zip(q, Q)], [a - b for a, b in zip(ref, Q)]).max() < 2e-5
+    parity.check("batch f32 o3-7 I", i, I, parity.F32_I, parity.ELEMENT_FACTOR * parity.F32_I)
+    parity.check("batch f32 o3-7 dQ", q, ref, parity.F32_INC, parity.ELEMENT_FACTOR * parity.F32_INC, base=Q)
 
 
 def test_uniform_batch_equals_solver(yt):

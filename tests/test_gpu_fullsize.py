@@ -8,6 +8,7 @@ import functools
 import numpy as np
 import pytest
 
+import parity
 import workload as wl
 from oracle import basis, scheme
 
@@ -78,11 +79,11 @@ def reference(order):
 # (the tensor-core form covers orders 2..6); tests of one order run consecutively so the
 # cached inputs and oracle results of that order are reused
 @pytest.mark.parametrize("order, prec_name, tol_q, tol_inc", [
-    (6, "YT_F64", 1e-12, 1e-11),
-    (6, "YT_F32", None, 2e-5),
-    (6, "YT_BF16X3_F32ACC", None, 1e-3),
-    (7, "YT_F64", 1e-12, 1e-11),
-    (7, "YT_F32", None, 2e-5),
+    (6, "YT_F64", parity.F64, parity.F64_INC),
+    (6, "YT_F32", None, parity.F32_INC),
+    (6, "YT_BF16X3_F32ACC", None, parity.TC_INC),
+    (7, "YT_F64", parity.F64, parity.F64_INC),
+    (7, "YT_F32", None, parity.F32_INC),
 ])
 def test_full_size_step_sampled(order, prec_name, tol_q, tol_inc):
     import paper_1903_11521_gb300 as yt
@@ -90,8 +91,8 @@ def test_full_size_step_sampled(order, prec_name, tol_q, tol_inc):
     ref = reference(order)
     got = gpu_sample(yt, order, el, conn, Q, dt, sample, getattr(yt, prec_name))
     q0 = Q[sample]
+    ef = 1.0 if prec_name == "YT_F64" else parity.ELEMENT_FACTOR
     if tol_q is not None:
-        assert rel_per_quantity(got, ref).max() < tol_q
-    err = rel_per_quantity(got - q0, ref - q0).max()
-    print(f"order {order} {prec_name}: increment error over {sample.size} sampled elements {err:.3e}")
-    assert err < tol_inc
+        parity.check(f"full size o{order} {prec_name} Q", got, ref, tol_q, tol_q)
+    parity.check(f"full size o{order} {prec_name} dQ ({sample.size} sampled)", got, ref, tol_inc,
+                 ef * tol_inc, base=q0)

@@ -155,3 +155,32 @@ def test_seissol_neighbour_chain_orders():
         pats3 = pats[:3] + [('slq', np.ones((S, B, 9), bool)), pats[4]]
         cost3, _ = es.strength_reduce('skp', pats3, names)
         assert es.tree_cost('skp', pats3, fused, names) == cost3
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_result_pattern_is_support_of_positive_einsum(seed):
+    """With positive values on the non-zeros (no cancellation possible), the boolean
+    result pattern is exactly the support of Eq. gentensorop's result; masking the
+    operands with their EQSPPs leaves the result pattern unchanged."""
+    rng = np.random.default_rng(100 + seed)
+    out, pats = _random_case(rng)
+    vals = [rng.uniform(0.5, 2.0, p.shape) * p for _, p in pats]
+    U = es.einsum_bruteforce(out, [(idx, v) for (idx, _), v in zip(pats, vals)])
+    P = es.result_pattern(out, pats)
+    assert P.dtype == bool and P.shape == U.shape
+    assert np.array_equal(P, U != 0)
+    hats = es.eqspp(out, pats)
+    assert np.array_equal(es.result_pattern(out, [(idx, h) for (idx, _), h in zip(pats, hats)]), P)
+
+
+def test_result_pattern_block_product():
+    """Block-diagonal times block-diagonal with matching blocks stays block-diagonal; with
+    the second operand's blocks swapped the product has the off-diagonal blocks."""
+    D = np.zeros((4, 4), dtype=bool)
+    D[:2, :2] = D[2:, 2:] = True
+    X = np.zeros((4, 4), dtype=bool)
+    X[:2, 2:] = X[2:, :2] = True
+    assert np.array_equal(es.result_pattern('ij', [('ik', D), ('kj', D)]), D)
+    assert np.array_equal(es.result_pattern('ij', [('ik', D), ('kj', X)]), X)
+    # an all-false operand gives an all-false result
+    assert not es.result_pattern('ij', [('ik', D), ('kj', np.zeros((4, 4), dtype=bool))]).any()
