@@ -36,6 +36,10 @@ struct yt_plan {
   int* d_prog = nullptr;
   void* d_consts = nullptr;
   std::vector<int> const_offset;       // per tensor, offset into consts (globals)
+  // host copy of the constants in the plan's precision (double or float values), built
+  // at creation: the source of every upload, alive as long as the plan
+  std::vector<unsigned char> consts_host;
+  size_t n_consts = 0;
   // scratch for temporaries, grown on demand
   mutable std::mutex mu;
   mutable void* scratch = nullptr;
@@ -262,17 +266,26 @@ void assign_const_offsets(yt_plan* p) {
     }
 }
 
+// The constants of all global tensors, in descriptor order, converted once to the plan's
+// precision.
+template <typename Real>
+void pack_consts(yt_plan* p) {
+  std::vector<Real> c;
+  for (size_t i = 0; i < p->tensors.size(); ++i)
+    if (p->tensors[i].global)
+      for (double v : p->tensors[i].values) c.push_back((Real)v);
+  p->n_consts = c.size();
+  if (c.empty()) c.push_back(Real(0));
+  p->consts_host.resize(c.size() * sizeof(Real));
+  std::memcpy(p->consts_host.data(), c.data(), p->consts_host.size());
+}
+
 // Device copies of the constants and the operation list, made on first execution.
 template <typename Real>
 void ensure_device(yt_plan* p) {
   if (p->d_ops) return;
-  std::vector<Real> consts;
-  for (size_t i = 0; i < p->tensors.size(); ++i)
-    if (p->tensors[i].global)
-      for (double v : p->tensors[i].values) consts.push_back((Real)v);
-  if (consts.empty()) consts.push_back(Real(0));
-  cuda_check(cudaMalloc(&p->d_consts, consts.size() * sizeof(Real)), "cudaMalloc consts");
-  cuda_check(cudaMemcpy(p->d_consts, consts.data(), consts.size() * sizeof(Real), cudaMemcpyHostToDevice), "copy consts");
+  cuda_check(cudaMalloc(&p->d_consts, p->consts_host.size()), "cudaMalloc consts");
+  cuda_check(cudaMemcpy(p->d_consts, p->consts_host.data(), p->consts_host.size(), cudaMemcpyHostToDevice), "copy consts");
   cuda_check(cudaMalloc(&p->d_prog, std::max<size_t>(1, p->prog.size()) * sizeof(int)), "cudaMalloc prog");
   if (!p->prog.empty())
     cuda_check(cudaMemcpy(p->d_prog, p->prog.data(), p->prog.size() * sizeof(int), cudaMemcpyHostToDevice), "copy prog");
@@ -376,6 +389,8 @@ extern "C" yt_status yt_plan_create(const char* expr, const yt_tensor_desc* tens
     p->expr = parse(expr, p->tensors);
     for (size_t t = 0; t < p->expr.terms.size(); ++t) p->terms.push_back(plan_term(p->expr, (int)t, p->tensors));
     assign_const_offsets(p.get());
+    if (precision == YT_F64) pack_consts<double>(p.get());
+    else pack_consts<float>(p.get());
     compile(p.get());
     *out = p.release();
   });
@@ -432,14 +447,20 @@ extern "C" yt_status yt_execute_batched(const yt_plan* p, void* const* element_t
 extern "C" void yt_plan_destroy(yt_plan* p) { delete p; }
 
 // ------------------------------------------------------ allocation-free execution
-// yt_execute_batched_noalloc runs the same executor kernel as yt_execute_batched, but
-// every device buffer it needs lives in the fixed-size file-scope arrays below, so the
-// call never allocates device memory.  The arrays are reserved on every device that
-// loads this library and stay reserved until the process exits.  All calls share them:
-// each call first copies the plan's operation list, index lists and constants into
-// them, and the temporaries are written before they are read, so nothing has to start
-// at zero.  Two calls whose work overlaps on the device (different streams, or devices
-// sharing nothing but this process) race on these arrays.
+// yt_execute_batched_noalloc computes what yt_execute_batched computes, but every device
+// buffer it needs lives in the fixed-size file-scope arrays below, so the call never
+// allocates device memory.  It always runs the lane-per-element executor kernel
+// (k_execute) with its temporaries in the fixed global scratch, also for the plans that
+// yt_execute_batched runs on the element-per-warp kernel (k_execute_ew, temporaries in
+// shared memory): that kernel needs a dynamic shared-memory size attribute set on the
+// function beyond 48 KB, which this entry point leaves alone.  Results agree with
+// yt_execute_batched up to the summation order; speed and the kernel named by a profiler
+// can differ.  The arrays are reserved on every device that loads this library and stay
+// reserved until the process exits.  All calls share them: each call first copies the
+// plan's operation list, index lists and constants into them (from host copies owned by
+// the plan), and the temporaries are written before they are read, so nothing has to
+// start at zero.  Two calls whose work overlaps on the device (different streams, or
+// devices sharing nothing but this process) race on these arrays.
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // temporaries: 32 MiB
@@ -489,11 +510,7 @@ void launch_noalloc(const yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t
              "plan index lists exceed the allocation-free limit of 2^20 integers");
   YT_REQUIRE(p->ops.size() <= kNoAllocOps, YT_ERR_UNSUPPORTED,
              "plan has more than 4096 operations");
-  std::vector<Real> consts;
-  for (size_t i = 0; i < p->tensors.size(); ++i)
-    if (p->tensors[i].global)
-      for (double v : p->tensors[i].values) consts.push_back((Real)v);
-  YT_REQUIRE(consts.size() * sizeof(Real) <= kNoAllocConstDoubles * sizeof(double), YT_ERR_UNSUPPORTED,
+  YT_REQUIRE(p->n_consts * sizeof(Real) <= kNoAllocConstDoubles * sizeof(double), YT_ERR_UNSUPPORTED,
              "plan constants exceed the allocation-free limit of 2 MiB");
   ExecPtrs<Real> T{};
   for (size_t i = 0; i < p->tensors.size(); ++i)
@@ -509,8 +526,9 @@ void launch_noalloc(const yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t
     cuda_check(cudaMemcpyAsync(a.prog, p->prog.data(), p->prog.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy prog");
   if (!p->ops.empty())
     cuda_check(cudaMemcpyAsync(a.ops, p->ops.data(), p->ops.size() * sizeof(ExecOp), cudaMemcpyHostToDevice, st), "copy ops");
-  if (!consts.empty())
-    cuda_check(cudaMemcpyAsync(a.consts, consts.data(), consts.size() * sizeof(Real), cudaMemcpyHostToDevice, st), "copy consts");
+  if (p->n_consts > 0)
+    cuda_check(cudaMemcpyAsync(a.consts, p->consts_host.data(), p->n_consts * sizeof(Real), cudaMemcpyHostToDevice, st),
+               "copy consts");
   const int64_t tiles = (n + 31) / 32;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>({(tiles + 3) / 4, (int64_t)sms * 8, (int64_t)(slots / 4)}));
   k_execute<Real><<<(unsigned)blocks, 128, 0, st>>>(static_cast<const ExecOp*>(a.ops), (int)p->ops.size(),
