@@ -50,6 +50,7 @@ class ServerStats(C.Structure):
 YT_F64, YT_F32, YT_BF16X3_F32ACC = 0, 1, 2
 YT_MEM_HOST, YT_MEM_DEVICE = 0, 1
 YT_FIELD_DOFS, YT_FIELD_TIME_INTEGRAL = 0, 1
+YT_SCHEME_DIAG_EXPIRE_WAIT = 1
 
 # every symbol declared in include/yateto_gb300.h with its (restype, argtypes)
 _P = C.c_void_p
@@ -89,6 +90,7 @@ SIGNATURES = {
     "yt_server_wait": (C.c_int, [_P, C.c_int64, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "yt_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "yt_server_destroy": (None, [_P]),
+    "yt_server_fail_tick": (C.c_int, [_P, C.c_int64]),
     "yt_reference_matrix": (C.c_int, [C.c_int32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "yt_tc_operands": (C.c_int, [C.c_int32, C.c_int32, _P, C.POINTER(C.c_int64)]),
     "yt_selftest_conversions": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),

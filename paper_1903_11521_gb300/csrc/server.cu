@@ -76,7 +76,8 @@ struct yt_server {
   size_t ref_capacity[8] = {};
   std::vector<TileRef> h_refs[8];
   bool refs_dirty = true;
-  std::string fatal;
+  std::string fatal;            // set when a tick failed: the server then fails every request
+  int64_t fail_at_tick = -1;    // diagnostics: a tick number treated as failed (host side)
   ~yt_server();
 };
 
@@ -111,9 +112,40 @@ void activate(yt_server* sv, Request* r) {
   std::vector<double>().swap(r->jacobian);
 }
 
+// After a failed tick the device state of the active solves is unknown: every active
+// solve is destroyed and its budget released, every pending request fails, and later
+// submissions are refused (sv->fatal).  Called with sv->mu held.
+void fail_all(yt_server* sv, const std::string& why) {
+  sv->fatal = why;
+  const double t = now_s();
+  for (Request* r : sv->active) {
+    if (r->solver) yt_solver_destroy(r->solver);
+    r->solver = nullptr;
+    sv->in_use -= r->bytes;
+    r->state = kFailed;
+    r->status = YT_ERR_CUDA;
+    r->error = why;
+    r->t_done = t;
+    ++sv->failed;
+  }
+  sv->active.clear();
+  for (Request* r : sv->pending) {
+    r->state = kFailed;
+    r->status = YT_ERR_CUDA;
+    r->error = "server stopped after a failed step: " + why;
+    r->t_done = t;
+    ++sv->failed;
+  }
+  sv->pending.clear();
+  sv->refs_dirty = true;
+  sv->cv_done.notify_all();
+}
+
 // One step of every active solve: per degree, one shared local and one shared neighbour
 // launch over the tile table of that degree's solves.
 void tick(yt_server* sv, const std::vector<Request*>& act) {
+  if (sv->fail_at_tick >= 0 && sv->ticks == sv->fail_at_tick)
+    throw Error(YT_ERR_CUDA, "injected failure of tick " + std::to_string(sv->ticks));
   std::vector<Request*> by_order[8];
   for (Request* r : act) by_order[r->order].push_back(r);
   for (int o = 2; o <= 7; ++o) {
@@ -216,17 +248,9 @@ void worker_loop(yt_server* sv) {
     try {
       tick(sv, act);
     } catch (const std::exception& e) {
+      for (int o = 2; o <= 7; ++o) (void)cudaStreamSynchronize(sv->streams[o]);
       std::lock_guard<std::mutex> lock(sv->mu);
-      sv->fatal = e.what();
-      for (Request* r : sv->active) {
-        r->state = kFailed;
-        r->status = YT_ERR_CUDA;
-        r->error = e.what();
-        r->t_done = now_s();
-        ++sv->failed;
-      }
-      sv->active.clear();
-      sv->cv_done.notify_all();
+      fail_all(sv, e.what());
       continue;
     }
     std::vector<Request*> finished;
@@ -304,6 +328,10 @@ extern "C" yt_status yt_server_submit(yt_server* sv, const yt_mesh_desc* mesh, i
     YT_REQUIRE(order >= 2 && order <= 7, YT_ERR_UNSUPPORTED, "order");
     YT_REQUIRE(n_steps > 0, YT_ERR_INVALID, "n_steps must be positive");
     YT_REQUIRE(dt > 0, YT_ERR_INVALID, "dt must be positive");
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      YT_REQUIRE(sv->fatal.empty(), YT_ERR_CUDA, "server stopped after a failed step: " + sv->fatal);
+    }
     auto r = std::make_unique<Request>();
     const int64_t E = mesh->n_elements;
     const size_t B = n_basis(order - 1);
@@ -360,6 +388,14 @@ extern "C" yt_status yt_server_stats_get(yt_server* sv, yt_server_stats* out) {
     out->budget_bytes = (int64_t)sv->budget;
     out->peak_bytes = (int64_t)sv->peak;
     out->element_updates = sv->element_updates;
+  });
+}
+
+extern "C" yt_status yt_server_fail_tick(yt_server* sv, int64_t at_tick) {
+  return guarded([&] {
+    YT_REQUIRE(sv, YT_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->fail_at_tick = at_tick;
   });
 }
 

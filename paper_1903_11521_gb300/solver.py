@@ -28,7 +28,7 @@ class Solver:
     or None.  DOFs are exchanged in the canonical layout [element][quantity][basis]."""
 
     def __init__(self, order, dt, material, jacobian, neighbours=None, faces=None,
-                 orient=None, precision=_lib.YT_F64, stream=None):
+                 orient=None, precision=_lib.YT_F64, stream=None, flags=0):
         self.lib = _lib.load()
         E = int(np.asarray(material).shape[0])
         self.n_elements = E
@@ -48,7 +48,7 @@ class Solver:
             desc.neighbours = _ptr(self._nb, C.c_int32)
             desc.faces = _ptr(self._fj, C.c_int8)
             desc.orient = _ptr(self._fh, C.c_int8)
-        sch = _lib.SchemeDesc(order=self.order, dt=float(dt), precision=precision, flags=0)
+        sch = _lib.SchemeDesc(order=self.order, dt=float(dt), precision=precision, flags=int(flags))
         handle = C.c_void_p()
         _lib.check(self.lib.yt_solver_create(C.byref(desc), C.byref(sch),
                                              _stream_handle(stream), C.byref(handle)),
@@ -256,6 +256,10 @@ class Server:
         _lib.check(self.lib.yt_server_wait(self.handle, rid, out.ctypes.data, C.byref(lat), C.byref(q)),
                    "yt_server_wait")
         return out.transpose(0, 2, 1), lat.value, q.value
+
+    def fail_tick(self, at_tick: int):
+        """Diagnostics: the worker treats its step `at_tick` as failed (host side)."""
+        _lib.check(self.lib.yt_server_fail_tick(self.handle, int(at_tick)), "yt_server_fail_tick")
 
     def stats(self) -> dict:
         st = _lib.ServerStats()

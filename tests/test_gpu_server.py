@@ -4,6 +4,7 @@ respect the HBM budget, and requests must actually share the device."""
 import numpy as np
 import pytest
 
+import parity
 import workload as wl
 from oracle import basis, scheme
 
@@ -72,8 +73,8 @@ def test_fp64_server_matches_oracle(yt):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     ref, _ = scheme.ader_step(r['Q'], star, loc, nb, r['neighbours'], r['faces'], r['orient'],
                               r['dt'], 3)
-    num = np.sqrt(((q - ref - 0) ** 2).sum((0, 1)))
-    assert (num / np.sqrt((ref ** 2).sum((0, 1)))).max() < 1e-12
+    parity.check("server f64 Q", q, ref, parity.F64, parity.F64)
+    parity.check("server f64 dQ", q, ref, parity.F64_INC, parity.F64_INC, base=r['Q'])
 
 
 def test_request_above_budget_fails(yt):
@@ -85,3 +86,42 @@ def test_request_above_budget_fails(yt):
         srv.wait(rid)
     assert info.value.status == 5
     srv.close()
+
+
+def test_failed_step_releases_everything(yt):
+    """A step that fails (injected on the host: the worker treats its step 2 as a failed
+    CUDA call; nothing faults on the device) ends the server's service: every active
+    and pending request fails with YT_ERR_CUDA, its waiter returns, the budget is given
+    back, later submissions are refused, and destroy returns."""
+    reqs = [make_request(4000 + 10 * i, 3 + i % 3, 300 + 50 * i) for i in range(6)]
+    budget = 24 * 2 ** 20          # about four of these (4-12 MB each) at a time; the rest wait
+    srv = yt.Server(budget, precision=yt.YT_F32)
+    srv.fail_tick(2)
+    ids = []
+    for r in reqs:
+        try:
+            ids.append(srv.submit(r['order'], r['dt'], r['material'], r['jacobian'], r['neighbours'],
+                                  r['faces'], r['orient'], r['Q'], 50))
+        except yt.YtError as e:      # the failure came before this submission: refused
+            assert e.status == 6
+    assert ids
+    for rid in ids:
+        with pytest.raises(yt.YtError) as info:
+            srv.wait(rid)
+        assert info.value.status == 6
+    st = srv.stats()
+    assert st['failed'] == len(ids) and st['completed'] == 0
+    assert st['active'] == 0 and st['pending'] == 0
+    r = reqs[0]
+    with pytest.raises(yt.YtError) as info:
+        srv.submit(r['order'], r['dt'], r['material'], r['jacobian'], r['neighbours'], r['faces'],
+                   r['orient'], r['Q'], 1)
+    assert info.value.status == 6
+    srv.close()
+    # a fresh server on the same device still computes the right result
+    srv = yt.Server(2 ** 30, precision=yt.YT_F32)
+    rid = srv.submit(r['order'], r['dt'], r['material'], r['jacobian'], r['neighbours'], r['faces'],
+                     r['orient'], r['Q'], 2)
+    q, _, _ = srv.wait(rid)
+    srv.close()
+    assert np.array_equal(q, solo(yt, r, 2, yt.YT_F32))
