@@ -136,7 +136,10 @@ yt_status yt_execute_batched(const struct yt_plan* plan, void* const* element_te
  * For callers that must not allocate device memory themselves or through libraries they
  * call: code whose device memory is owned by a host framework's own pool, or loops that
  * must not take the device-wide synchronisation that cudaMalloc / cudaFree can imply.
- * Same arguments and results as yt_execute_batched.  It calls no cudaMalloc, cudaFree or
+ * Same arguments and results as yt_execute_batched (up to the summation order): it always
+ * runs the lane-per-element executor kernel with the temporaries in global scratch, also
+ * for plans that yt_execute_batched runs on its element-per-warp kernel with the
+ * temporaries in shared memory, so its speed can differ.  It calls no cudaMalloc, cudaFree or
  * allocating routine: the plan's operation list, index lists, constants and the
  * temporaries live in fixed arrays inside the library (reserved on every device that
  * loads it, until process exit): temporaries 32 MiB, index lists 2^20 integers, 4096
@@ -144,8 +147,8 @@ yt_status yt_execute_batched(const struct yt_plan* plan, void* const* element_te
  * YT_ERR_UNSUPPORTED and a message naming the limit; nothing runs then.  The first call
  * on each device looks up the arrays' device addresses (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  Every call copies the
- * plan's tables into the shared arrays (from host memory, on `stream`) and then runs the
- * kernel; calls whose work overlaps on the device, e.g. on two streams, race on the
+ * plan's tables into the shared arrays (from host copies that the plan owns, on `stream`)
+ * and then runs the kernel; calls whose work overlaps on the device, e.g. on two streams, race on the
  * shared arrays and must be serialised by the caller. */
 yt_status yt_execute_batched_noalloc(const struct yt_plan* plan, void* const* element_tensors,
                                      int64_t n_elements, yt_stream stream);
@@ -181,8 +184,15 @@ typedef struct yt_scheme_desc {
   int32_t order;             /* convergence order O = N + 1: 2..7 */
   double dt;                 /* time step */
   yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7), YT_BF16X3_F32ACC (2..6) */
-  int32_t flags;             /* reserved, must be 0 */
+  int32_t flags;             /* 0, or YT_SCHEME_DIAG_EXPIRE_WAIT */
 } yt_scheme_desc;
+/* Diagnostics flag (no counterpart in the paper), YT_BF16X3_F32ACC solvers only: the
+ * tensor-core local kernel does not issue its operand load and its first bounded wait
+ * (on that load) gives up after 1 ms, before any tensor-core or bulk-copy operation is
+ * in flight; the kernel then issues nothing, frees its tensor memory and records the
+ * timeout, which yt_solver_status reports as YT_ERR_TIMEOUT.  The outputs of such a step
+ * are meaningless.  For testing the timeout path without a fault or a hang. */
+#define YT_SCHEME_DIAG_EXPIRE_WAIT 1
 
 struct yt_solver;
 
@@ -307,6 +317,13 @@ yt_status yt_server_wait(struct yt_server* server, int64_t request_id, double* d
 yt_status yt_server_stats_get(struct yt_server* server, yt_server_stats* out);
 /* Finishes every submitted request, then stops the worker and frees the server. */
 void yt_server_destroy(struct yt_server* server);
+/* Diagnostics (no counterpart in the paper): the worker treats its step number `at_tick`
+ * (0 = the first; -1 = none) as failed, as if a CUDA call in it had returned an error,
+ * without touching the device.  A failed step ends the server's service: the active
+ * solves are freed and fail with YT_ERR_CUDA, pending requests fail, and later
+ * yt_server_submit calls return YT_ERR_CUDA; yt_server_wait and yt_server_destroy still
+ * return.  For testing that failure path. */
+yt_status yt_server_fail_tick(struct yt_server* server, int64_t at_tick);
 
 /* Host-only diagnostics: the global-matrix operands of the tensor-core kernels of an order
  * (2..6) as uploaded by a YT_BF16X3_F32ACC solver; kernel 0 = the local kernel (passes:

@@ -100,6 +100,7 @@ void set_attributes() {
 tc::TcStep step_of(const tc::TcLaunch& L) {
   tc::TcStep T;
   T.dt = L.dt;
+  T.expire_first_wait = L.expire_first_wait;
   double f = 1.0;
   for (int i = 0; i < 8; ++i) {
     f *= (i + 1.0);

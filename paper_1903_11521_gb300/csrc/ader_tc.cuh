@@ -205,11 +205,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait for phase `parity` of `bar`: false after kTcWaitNs.
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`: false after `limit_ns` (default kTcWaitNs).
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kTcWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_timer();
-  while (global_timer() - t0 < kTcWaitNs)
+  while (global_timer() - t0 < limit_ns)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -288,7 +288,10 @@ __device__ __forceinline__ void issue_group(int g, uint32_t tmem, int cs, uint32
 struct TcStep {
   double dt;
   double invfact[8];
+  int expire_first_wait;     // diagnostics: the operand load is not issued and its wait
+                             // gives up after kDiagWaitNs (nothing is in flight then)
 };
+constexpr unsigned long long kDiagWaitNs = 1000000ull;    // 1 ms
 
 // Per-CTA resources: tensor memory, two mbarriers (operand load, MMA completion).
 struct TcShared {
@@ -370,8 +373,8 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   fence_after_sync();
   const uint32_t tmem = ts->tmem;
   const bool issuer = lane == 0 && w < 3;          // issues accumulator group w
-  if (leader) load_operands(opb, blob, L::BLOB, bar_ld);
-  bool ok = __syncthreads_and(tc_wait(bar_ld, 0)) != 0;
+  if (leader && !T.expire_first_wait) load_operands(opb, blob, L::BLOB, bar_ld);
+  bool ok = __syncthreads_and(tc_wait(bar_ld, 0, T.expire_first_wait ? kDiagWaitNs : kTcWaitNs)) != 0;
   uint32_t phase = 0;
   bool pending = false;              // a commit whose wait timed out
   uint32_t pending_phase = 0;
@@ -839,6 +842,7 @@ struct TcLaunch {
   double dt;
   StarPattern SP;
   int* status;
+  int expire_first_wait;     // diagnostics (YT_SCHEME_DIAG_EXPIRE_WAIT)
   cudaStream_t stream;
 };
 

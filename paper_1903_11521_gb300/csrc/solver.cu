@@ -286,6 +286,7 @@ tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt =
   L.dt = s->dt;
   L.SP = kStar;
   L.status = s->d_status;
+  L.expire_first_wait = s->diag_expire_wait ? 1 : 0;
   L.stream = st;
   return L;
 }
@@ -487,7 +488,9 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     *out = nullptr;
     YT_REQUIRE(mesh->n_elements > 0 && mesh->material && mesh->jacobian, YT_ERR_INVALID,
                "mesh needs n_elements > 0, material and jacobian");
-    YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
+    YT_REQUIRE((scheme->flags & ~YT_SCHEME_DIAG_EXPIRE_WAIT) == 0, YT_ERR_INVALID, "unknown scheme flags");
+    YT_REQUIRE(scheme->flags == 0 || scheme->precision == YT_BF16X3_F32ACC, YT_ERR_INVALID,
+               "YT_SCHEME_DIAG_EXPIRE_WAIT needs YT_BF16X3_F32ACC (the kernels with bounded waits)");
     YT_REQUIRE(scheme->order >= 2 && scheme->order <= 7, YT_ERR_INVALID, "order must be 2..7");
     YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32 ||
                    scheme->precision == YT_BF16X3_F32ACC,
@@ -509,6 +512,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     s->real_bytes = s->prec == YT_F64 ? sizeof(double) : sizeof(float);
     s->dt = scheme->dt;
     s->has_neighbours = nb;
+    s->diag_expire_wait = (scheme->flags & YT_SCHEME_DIAG_EXPIRE_WAIT) != 0;
     std::vector<int> conn;
     if (nb) {
       conn.assign((size_t)s->Epad * 4, 0);

@@ -34,6 +34,7 @@ struct yt_solver {
   float* d_tc_scratch = nullptr;
   int* d_status = nullptr;
   unsigned tc_grid = 0;
+  bool diag_expire_wait = false;     // YT_SCHEME_DIAG_EXPIRE_WAIT
   // yt_step_host: copy stream and per-chunk events (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
