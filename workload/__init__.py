@@ -72,6 +72,41 @@ def random_dofs(n_elements: int, n_basis: int, seed: int = SEED + 1, scale: str 
     return Q
 
 
+@dataclass
+class Attenuation:
+    omega: np.ndarray     # (E, 3) relaxation frequencies of the three mechanisms
+    ylam: np.ndarray      # (E, 3) anelastic moduli Y^lambda_l
+    ymu: np.ndarray       # (E, 3) anelastic moduli Y^mu_l
+
+
+def attenuation(elements: Elements, dt: float, seed: int = SEED + 900,
+                omega_dt=(0.005, 0.05, 0.5), y: float = 0.02) -> Attenuation:
+    """Synthetic parameters of three attenuation mechanisms per element (the paper gives
+    none): omega_l dt = omega_dt[l] x U[0.8, 1.25] (a band of two decades around
+    omega dt = 0.05, so that relaxation is resolved by the step), Y_l = y x U[0.5, 1.5] x
+    (lambda, mu) (a weak attenuation, quality factor of order 1 / y)."""
+    rng = _rng(seed)
+    E = elements.rho.shape[0]
+    omega = np.asarray(omega_dt)[None, :] * rng.uniform(0.8, 1.25, (E, 3)) / dt
+    fy = y * rng.uniform(0.5, 1.5, (E, 3))
+    return Attenuation(omega, fy * elements.lam[:, None], fy * elements.mu[:, None])
+
+
+def random_dofs_viscoelastic(n_elements: int, n_basis: int, elements: Elements,
+                             att: Attenuation, seed: int = SEED + 901) -> np.ndarray:
+    """Q (E, B, 27): elastic part as random_dofs(..., "impedance"); the anelastic
+    functions of mechanism l (units of stress per time) ~ N(0,1) rho c_p omega_l, so that
+    their feedback into the stresses over one step is of the size of the elastic
+    increment."""
+    rng = _rng(seed)
+    Q = rng.standard_normal((n_elements, n_basis, 27))
+    z = elements.rho * np.sqrt((elements.lam + 2 * elements.mu) / elements.rho)
+    Q[:, :, :6] *= z[:, None, None]
+    for l in range(3):
+        Q[:, :, 9 + 6 * l:15 + 6 * l] *= (z * att.omega[:, l])[:, None, None]
+    return Q
+
+
 def random_connectivity(n_elements: int, seed: int = SEED + 2) -> Connectivity:
     """Random perfect matching of the 4E face slots (no element paired with itself)."""
     if n_elements < 2:
