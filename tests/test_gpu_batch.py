@@ -83,8 +83,8 @@ def test_mixed_orders_fp32_up_to_order7(yt):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     ref, I = scheme.ader_step_mixed(Q, orders - 1, star, loc, nb, conn.neighbours, conn.faces,
                                     conn.orient, dt)
-    parity.check("batch f32 o3-7 I", i, I, parity.F32_I, parity.ELEMENT_FACTOR * parity.F32_I)
-    parity.check("batch f32 o3-7 dQ", q, ref, parity.F32_INC, parity.ELEMENT_FACTOR * parity.F32_INC, base=Q)
+    parity.check("batch f32 o3-7 I", i, I, parity.F32_I, parity.F32_I_EL)
+    parity.check("batch f32 o3-7 dQ", q, ref, parity.F32_INC, parity.F32_INC_EL, base=Q)
 
 
 def test_uniform_batch_equals_solver(yt):

@@ -91,8 +91,9 @@ def test_full_size_step_sampled(order, prec_name, tol_q, tol_inc):
     ref = reference(order)
     got = gpu_sample(yt, order, el, conn, Q, dt, sample, getattr(yt, prec_name))
     q0 = Q[sample]
-    ef = 1.0 if prec_name == "YT_F64" else parity.ELEMENT_FACTOR
+    tol_el = {"YT_F64": parity.F64_INC, "YT_F32": parity.F32_INC_EL,
+              "YT_BF16X3_F32ACC": parity.TC_INC_EL}[prec_name]
     if tol_q is not None:
         parity.check(f"full size o{order} {prec_name} Q", got, ref, tol_q, tol_q)
     parity.check(f"full size o{order} {prec_name} dQ ({sample.size} sampled)", got, ref, tol_inc,
-                 ef * tol_inc, base=q0)
+                 tol_el, base=q0)

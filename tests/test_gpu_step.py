@@ -13,7 +13,6 @@ from oracle import basis, planewave, scheme
 
 pytestmark = pytest.mark.gpu
 TOL = parity.F64
-EF = parity.ELEMENT_FACTOR
 
 
 @pytest.fixture(scope="module")
@@ -206,8 +205,8 @@ def test_f32_full_step_against_fp64_oracle(yt, order):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     q_ref, I = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
                                 dt, order - 1)
-    parity.check(f"f32 step o{order} I", i32, I, F32_TOL_I, EF * F32_TOL_I)
-    parity.check(f"f32 step o{order} dQ", q32, q_ref, F32_TOL_INCREMENT, EF * F32_TOL_INCREMENT, base=Q)
+    parity.check(f"f32 step o{order} I", i32, I, F32_TOL_I, parity.F32_I_EL)
+    parity.check(f"f32 step o{order} dQ", q32, q_ref, F32_TOL_INCREMENT, parity.F32_INC_EL, base=Q)
 
 
 def test_f32_local_step_order7(yt):
@@ -216,8 +215,8 @@ def test_f32_local_step_order7(yt):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     _, I = scheme.derivatives_and_time_integral(Q, star, dt, 6)
     q_ref = scheme.local_update(Q, I, star, loc, 6)
-    parity.check("f32 local o7 I", i32, I, F32_TOL_I, EF * F32_TOL_I)
-    parity.check("f32 local o7 dQ", q32, q_ref, F32_TOL_INCREMENT, EF * F32_TOL_INCREMENT, base=Q)
+    parity.check("f32 local o7 I", i32, I, F32_TOL_I, parity.F32_I_EL)
+    parity.check("f32 local o7 dQ", q32, q_ref, F32_TOL_INCREMENT, parity.F32_INC_EL, base=Q)
 
 
 def test_f32_plane_wave_100_steps(yt):
@@ -246,7 +245,8 @@ def test_f32_order7_100_steps_against_oracle(yt):
     mesh against 100 oracle steps.  The wave has quantities of zero exact amplitude
     (sigma_yz, sigma_xz, w) whose norms sit at the discretisation-error level, so the error
     of each quantity is stated relative to the norm of the whole solution (unit material:
-    stresses and velocities of one magnitude): bound 1e-4."""
+    stresses and velocities of one magnitude): bound 5e-6 (measured 6.0e-7), per element
+    1.5e-5 (measured 1.6e-6)."""
     order, N = 7, 6
     k = 2 * np.pi * np.array([1.0, 1.0, 0.0])
     mesh = wl.periodic_cube_mesh(3)
@@ -261,14 +261,14 @@ def test_f32_order7_100_steps_against_oracle(yt):
     per_q = np.sqrt(((q32 - Q) ** 2).sum(axis=(0, 1)))
     err = per_q.max() / np.sqrt((Q ** 2).sum())
     el_err = parity.per_element(q32, Q).max()
-    print(f"PARITY f32 o7 100 steps: {err:.3e} of the solution norm (bound 1e-4), per-element "
-          f"{el_err:.3e} (bound 1e-3); per quantity {np.array2string(rel_per_quantity(q32, Q), precision=2)}")
-    assert err < 1e-4
-    assert el_err < 1e-3
+    print(f"PARITY f32 o7 100 steps: {err:.3e} of the solution norm (bound 5e-6), per-element "
+          f"{el_err:.3e} (bound 1.5e-5); per quantity {np.array2string(rel_per_quantity(q32, Q), precision=2)}")
+    assert err < 5e-6
+    assert el_err < 1.5e-5
 
 
-@pytest.mark.parametrize("prec_name, tol_inc", [("YT_F64", parity.F64_INC), ("YT_F32", parity.F32_INC),
-                                                ("YT_BF16X3_F32ACC", parity.TC_INC)])
+@pytest.mark.parametrize("prec_name, tol_inc", [("YT_F64", parity.F64_INC), ("YT_F32", parity.F32_INC_EL),
+                                                ("YT_BF16X3_F32ACC", parity.TC_INC_EL)])
 def test_single_element_self_neighbour(yt, prec_name, tol_inc):
     """Degenerate connectivity: one element (one tile of 32 lanes with 31 padding lanes)
     whose four faces are its own neighbours (faces paired 0-3 and 1-2, all orientations):
@@ -306,13 +306,15 @@ def test_zero_dofs_stay_zero(yt):
         s.close()
 
 
-@pytest.mark.parametrize("prec_name, order, tol", [("YT_F64", 6, 1e-12), ("YT_F64", 7, 1e-12),
-                                                   ("YT_F32", 7, 1e-5), ("YT_BF16X3_F32ACC", 6, 1e-4)])
-def test_jittered_structured_mesh_steps(yt, prec_name, order, tol):
+@pytest.mark.parametrize("prec_name, order, tol, tol_el", [
+    ("YT_F64", 6, 1e-12, 1e-11), ("YT_F64", 7, 1e-12, 1e-11),
+    ("YT_F32", 7, 1e-6, 3.5e-6), ("YT_BF16X3_F32ACC", 6, 4e-5, 1e-4)])
+def test_jittered_structured_mesh_steps(yt, prec_name, order, tol, tol_el):
     """Three steps on the jittered periodic structured mesh (vertices moved by up to 0.1 h,
     the mesh family of the order-7 FP32 workload) against three oracle steps, random
     impedance-scaled DOFs; error per quantity relative to the norm of the whole solution
-    change (stated bounds: FP64 1e-12, FP32 1e-5, split-bf16 1e-4)."""
+    change (stated bounds: FP64 1e-12, FP32 1e-6, split-bf16 4e-5, about nine times the
+    measured 1.2e-7 and 3.8e-6; per element 1e-11, 3.5e-6, 1e-4)."""
     N = order - 1
     mesh = wl.jittered_periodic_mesh(3, jitter=0.1, seed=17)
     el = mesh.elements
@@ -327,9 +329,9 @@ def test_jittered_structured_mesh_steps(yt, prec_name, order, tol):
     err = np.sqrt(((q - Q) ** 2).sum(axis=(0, 1))).max() / np.sqrt(((Q - Q0) ** 2).sum())
     el_err = parity.per_element(q - Q0, Q - Q0).max()
     print(f"PARITY {prec_name} jittered o{order} 3 steps: {err:.3e} (bound {tol:.1e}), "
-          f"per-element {el_err:.3e} (bound {EF * tol:.1e})")
+          f"per-element {el_err:.3e} (bound {tol_el:.1e})")
     assert err < tol, err
-    assert el_err < EF * tol, el_err
+    assert el_err < tol_el, el_err
 
 
 def _nonzero_flops(order):

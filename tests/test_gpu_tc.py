@@ -15,7 +15,6 @@ pytestmark = pytest.mark.gpu
 
 TC_TOL_I = parity.TC_I            # time integral
 TC_TOL_INCREMENT = parity.TC_INC  # Q_new - Q
-EF = parity.ELEMENT_FACTOR
 
 
 @pytest.fixture(scope="module")
@@ -59,8 +58,8 @@ def test_tc_full_step_against_fp64_oracle(yt, order):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     q_ref, I = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
                                 dt, order - 1)
-    parity.check(f"tc step o{order} I", i, I, TC_TOL_I, EF * TC_TOL_I)
-    parity.check(f"tc step o{order} dQ", q, q_ref, TC_TOL_INCREMENT, EF * TC_TOL_INCREMENT, base=Q)
+    parity.check(f"tc step o{order} I", i, I, TC_TOL_I, parity.TC_I_EL)
+    parity.check(f"tc step o{order} dQ", q, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
 
 
 @pytest.mark.parametrize("order", [3, 6])
@@ -75,8 +74,8 @@ def test_tc_local_step(yt, order):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     _, I = scheme.derivatives_and_time_integral(Q, star, dt, order - 1)
     q_ref = scheme.local_update(Q, I, star, loc, order - 1)
-    parity.check(f"tc local o{order} I", i, I, TC_TOL_I, EF * TC_TOL_I)
-    parity.check(f"tc local o{order} dQ", q, q_ref, TC_TOL_INCREMENT, EF * TC_TOL_INCREMENT, base=Q)
+    parity.check(f"tc local o{order} I", i, I, TC_TOL_I, parity.TC_I_EL)
+    parity.check(f"tc local o{order} dQ", q, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
 
 
 def test_tc_many_tiles_and_phases(yt):
@@ -103,7 +102,7 @@ def test_tc_many_tiles_and_phases(yt):
     q_ref, _ = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
                                 dt, order - 1)
     for mode, out in zip(("step", "phases", "unfused"), outs):
-        parity.check(f"tc many tiles {mode} dQ", out, q_ref, TC_TOL_INCREMENT, EF * TC_TOL_INCREMENT, base=Q)
+        parity.check(f"tc many tiles {mode} dQ", out, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
 
 
 def test_tc_deterministic(yt):
@@ -119,8 +118,9 @@ def test_tc_deterministic(yt):
 
 def test_tc_plane_wave_100_steps(yt):
     """100 steps at order 5 on the periodic mesh: drift from the FP64 path within a stated
-    bound (1e-2 per quantity; measured 3.8e-3), plane-wave error equal to the FP64 one to
-    5e-2 relative."""
+    bound (1e-2 per quantity, measured 3.8e-3: the quantities of zero exact amplitude carry
+    the largest relative drift; 3e-4 per element, measured 3.5e-5), plane-wave error equal
+    to the FP64 one to 5e-2 relative."""
     order, N = 5, 4
     k = 2 * np.pi * np.array([1.0, 1.0, 0.0])
     mesh = wl.periodic_cube_mesh(3)
@@ -141,9 +141,9 @@ def test_tc_plane_wave_100_steps(yt):
         s.close()
     drift = rel_per_quantity(out[yt.YT_BF16X3_F32ACC], out[yt.YT_F64]).max()
     el_drift = parity.per_element(out[yt.YT_BF16X3_F32ACC], out[yt.YT_F64]).max()
-    print(f"PARITY tc plane wave 100 steps drift {drift:.3e} (bound 1e-2), per-element {el_drift:.3e} (bound 1e-1)")
+    print(f"PARITY tc plane wave 100 steps drift {drift:.3e} (bound 1e-2), per-element {el_drift:.3e} (bound 3e-4)")
     assert drift < 1e-2
-    assert el_drift < 1e-1
+    assert el_drift < 3e-4
     e64 = planewave.l2_error(mesh, N, out[yt.YT_F64], T, k, 1.0, 2.0, 1.0)
     etc = planewave.l2_error(mesh, N, out[yt.YT_BF16X3_F32ACC], T, k, 1.0, 2.0, 1.0)
     print("plane-wave error fp64", e64, "tensor-core", etc)
@@ -180,4 +180,4 @@ def test_bounded_wait_runs_out_and_reports_timeout(yt):
     star, loc, nb = scheme.setup_element_matrices(el.rho, el.lam, el.mu, el.jac)
     q_ref, _ = scheme.ader_step(Q, star, loc, nb, conn.neighbours, conn.faces, conn.orient,
                                 dt, order - 1)
-    parity.check("tc after timeout dQ", q, q_ref, TC_TOL_INCREMENT, EF * TC_TOL_INCREMENT, base=Q)
+    parity.check("tc after timeout dQ", q, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
