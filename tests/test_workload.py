@@ -49,3 +49,16 @@ def test_jitter_is_seeded():
     c = wl.jittered_periodic_mesh(3, jitter=0.1, seed=12)
     assert np.array_equal(a.vertices, b.vertices)
     assert not np.array_equal(a.vertices, c.vertices)
+
+
+@pytest.mark.parametrize("E, seed", [(45, 508), (2, 1), (3, 7), (64, 3), (1000, 1905)])
+def test_random_connectivity_is_an_involution(E, seed):
+    """Every face slot is paired with exactly one other slot of another element, and the
+    pairing is symmetric (the neighbour's neighbour is the element itself)."""
+    c = wl.random_connectivity(E, seed=seed)
+    assert c.neighbours.min() >= 0 and c.neighbours.max() < E
+    assert (c.neighbours != np.arange(E)[:, None]).all()
+    assert ((c.faces >= 0) & (c.faces < 4)).all()
+    back = c.neighbours[c.neighbours, c.faces]
+    assert (back == np.arange(E)[:, None]).all()
+    assert (c.faces[c.neighbours, c.faces] == np.arange(4)[None, :]).all()

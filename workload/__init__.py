@@ -119,7 +119,9 @@ def random_connectivity(n_elements: int, seed: int = SEED + 2) -> Connectivity:
         if self_pair.size == 0:
             break
         other = rng.integers(0, a.size, self_pair.size)
-        b[self_pair], b[other] = b[other].copy(), b[self_pair].copy()
+        # one swap at a time: a permutation also when the draws repeat or hit a self pair
+        for i, o in zip(self_pair, other):
+            b[i], b[o] = b[o], b[i]
     else:
         raise RuntimeError("could not remove self pairs")
     nb = np.empty(4 * n_elements, dtype=np.int64)
