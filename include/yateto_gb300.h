@@ -178,6 +178,8 @@ typedef struct yt_mesh_desc {
                                 a local-only solver (yt_step_neighbour then fails) */
   const int8_t* faces;       /* host, E x 4: the neighbour's face index j (0..3) */
   const int8_t* orient;      /* host, E x 4: orientation h (0..2) */
+  const double* attenuation; /* host, E x 3 x 3: (omega_l, Y^lambda_l, Y^mu_l) of the
+                                mechanisms l = 0..2, for 27-quantity solvers; else NULL */
 } yt_mesh_desc;
 
 typedef struct yt_scheme_desc {
@@ -185,7 +187,23 @@ typedef struct yt_scheme_desc {
   double dt;                 /* time step */
   yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7), YT_BF16X3_F32ACC (2..6) */
   int32_t flags;             /* 0, or YT_SCHEME_DIAG_EXPIRE_WAIT */
+  int32_t quantities;        /* 9 (or 0): elastic; 27: viscoelastic-shaped (below) */
 } yt_scheme_desc;
+/* 27-quantity solvers (YT_F64 or YT_F32, orders 2..7).  The paper names viscoelastic
+ * attenuation with three mechanisms (27 quantities, Sec. 5.1) without its equations; this
+ * library reads it as the memory-variable form q = (sigma, v, theta^0, theta^1, theta^2),
+ * q_t + A q_x + B q_y + C q_z = E q, with six anelastic functions theta^l per mechanism:
+ *   - the rows of theta^l in A, B, C are omega_l times the stress-velocity rows of the
+ *     elastic Jacobian with the moduli (Y^lambda_l, Y^mu_l); their columns are zero;
+ *   - E: d sigma_i/dt gets -sum_l theta^l_i, d theta^l_i/dt gets -omega_l theta^l_i.
+ * The step is the elastic one with D^{d+1} += D^d E^T in the CK recursion and Q += I E^T
+ * in the update (the source enters through the time-integrated DOFs); star matrices and
+ * upwind flux solvers are those of the 27 x 27 Jacobians (|A_n| = a A_n^2 + b A_n^4 on
+ * the same spectrum).  Quantity order in every DOF array: the 9 elastic ones, then
+ * theta^l_i at 9 + 6 l + i.  yt_step, yt_step_phase (phase 1 runs two kernels: the
+ * elastic neighbour flux and the anelastic rows' volume, source and fluxes) and
+ * yt_step_host are available; yt_step_local / yt_step_neighbour, batches and servers are
+ * elastic only (YT_ERR_UNSUPPORTED). */
 /* Diagnostics flag (no counterpart in the paper), YT_BF16X3_F32ACC solvers only: the
  * tensor-core local kernel does not issue its operand load and its first bounded wait
  * (on that load) gives up after 1 ms, before any tensor-core or bulk-copy operation is
@@ -201,9 +219,9 @@ struct yt_solver;
  * is allocated here; DOFs start at zero. */
 yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
                            yt_stream stream, struct yt_solver** out_solver);
-/* Copies Q in: `dofs` holds E x 9 x B values in the canonical element layout
- * [element][quantity][basis] (basis index fastest, column-major B x 9 per element), as
- * double, in host or device memory (`where`).  Asynchronous on `stream`; host memory must
+/* Copies Q in: `dofs` holds E x P x B values (P = the solver's quantities, 9 or 27) in
+ * the canonical element layout [element][quantity][basis] (basis index fastest,
+ * column-major B x P per element), as double, in host or device memory (`where`).  Asynchronous on `stream`; host memory must
  * stay valid until the stream reaches this point (use pinned memory to overlap). */
 yt_status yt_solver_set_dofs(struct yt_solver* solver, const double* dofs, yt_memory where,
                              yt_stream stream);

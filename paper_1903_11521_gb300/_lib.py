@@ -29,12 +29,13 @@ class PlanStats(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("n_elements", C.c_int64), ("material", C.POINTER(C.c_double)),
                 ("jacobian", C.POINTER(C.c_double)), ("neighbours", C.POINTER(C.c_int32)),
-                ("faces", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8))]
+                ("faces", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8)),
+                ("attenuation", C.POINTER(C.c_double))]
 
 
 class SchemeDesc(C.Structure):
     _fields_ = [("order", C.c_int32), ("dt", C.c_double), ("precision", C.c_int),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("quantities", C.c_int32)]
 
 
 class ServerDesc(C.Structure):

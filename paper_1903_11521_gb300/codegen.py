@@ -188,6 +188,8 @@ def emit_rows(N, lst, nvals):
 
 VARIANTS = {"lf": ("true", "true"), "ll": ("true", "false"), "nf": ("false", "true"),
             "np": ("false", "false")}
+# kernels of a 27-quantity step: local (VE), neighbour flux of the elastic rows, anelastic rows
+VE_VARIANTS = {"vl": 0, "vn": 1, "vt": 2}
 
 UNIT = """// Generated by codegen.py: one kernel variant ({V}) of polynomial degree {N},
 // contraction type {REAL}.
@@ -197,6 +199,18 @@ UNIT = """// Generated by codegen.py: one kernel variant ({V}) of polynomial deg
 namespace yt {{
 void ader_set_attribute_o{N}_{P}_{V}(size_t smem) {{ ader_set_attribute<{N}, {REAL}, {LOCAL}, {FUSED}>(smem); }}
 void ader_launch_o{N}_{P}_{V}(const AderLaunch& L) {{ ader_launch<{N}, {REAL}, {LOCAL}, {FUSED}>(L); }}
+int ader_upload_o{N}_{P}_{V}(const float* vals, size_t n) {{ {UPLOAD} }}
+}}  // namespace yt
+"""
+
+VE_UNIT = """// Generated by codegen.py: one kernel of a 27-quantity step ({V}) of polynomial degree
+// {N}, contraction type {REAL}.
+#include "ader_kernels.cuh"
+#include "yt_rows_o{N}.cuh"
+
+namespace yt {{
+void ader_set_attribute_o{N}_{P}_{V}(size_t smem) {{ ader_set_attribute_ve<{N}, {REAL}, {WHICH}>(smem); }}
+void ader_launch_o{N}_{P}_{V}(const AderLaunch& L) {{ ader_launch_ve<{N}, {REAL}, {WHICH}>(L); }}
 int ader_upload_o{N}_{P}_{V}(const float* vals, size_t n) {{ {UPLOAD} }}
 }}  // namespace yt
 """
@@ -239,6 +253,15 @@ def generate(build_dir: str) -> list[str]:
                 upload = "(void)vals; (void)n; return 0;"
             _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused, UPLOAD=upload,
                                                 REAL="double" if P == "f64" else "float"))
+            units.append(unit)
+        for V, which in VE_VARIANTS.items():
+            unit = os.path.join(gen, f"ader_o{N}_{P}_{V}.cu")
+            if P == "f32" and N <= CONST_MAX_N:
+                upload = (f"return (int)cudaMemcpyToSymbol(gen::c_vals_o{N}, vals, n * sizeof(float));")
+            else:
+                upload = "(void)vals; (void)n; return 0;"
+            _write_if_changed(unit, VE_UNIT.format(N=N, P=P, V=V, WHICH=which, UPLOAD=upload,
+                                                   REAL="double" if P == "f64" else "float"))
             units.append(unit)
     info = os.path.join(gen, "ader_gen_info.cu")
     cases = "\n".join(f"    case {n}: return {c};" for n, c in counts.items())

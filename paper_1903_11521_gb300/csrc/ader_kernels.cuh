@@ -175,6 +175,23 @@ struct TileRef {
   double dt;
 };
 
+// 27-quantity (viscoelastic-shaped) steps: q = (9 elastic quantities, theta^l_i at
+// 9 + 6 l + i for three mechanisms l and six components i).  The anelastic functions
+// carry no flux (their columns of the Jacobians are zero) and are driven by the
+// velocities through the rows of the star matrices Astar^x_{theta,q}, which have the
+// slot pattern of the stress rows (columns 6..8); the source E couples them:
+// d sigma_i/dt -= sum_l theta^l_i, d theta^l_i/dt -= omega_l theta^l_i.  Warp i < 6 (the
+// stress row i) owns theta^l_i of its lane's element in k_local.
+constexpr int kNqVe = 27;
+constexpr int kNTheta = 18;
+constexpr int kStressSlots = 15;       // star slots of the six stress rows
+template <typename Real>
+struct VeTables {
+  Real* theta;          // [tile][18][B][32] current scaled derivative D~^d of theta (scratch)
+  const Real* cth;      // [tile][3 mech][3 dir][15 stress slots][32] Astar^x rows of theta^l
+  const Real* om;       // [tile][3][32] omega_l
+};
+
 // Where k_local keeps the operand column of its sparse products (D~^delta, then I): rows
 // in registers make every non-zero one fma with a register operand (the binary64
 // time-integral accumulator then lives in shared memory, touched once per row and
@@ -240,6 +257,39 @@ __device__ __forceinline__ Real row_op(const Real* __restrict__ v, const Real (&
 // processed in increasing order overwrite rows that are no longer needed.  The time
 // integral accumulates in double registers; only the C(N+2,3) rows that receive
 // derivative terms need one (rows of degree N hold c0 Q alone).
+// One row K of a derivative of a 27-quantity step, stress warp w: the feedback of the
+// anelastic functions into the stress (E_{sigma_i, theta^l_i} = -1) is added to v, and
+// D~^{d+1}[K][theta^l_w] = dt (sum_x sum_q Astar^x_{theta,q} X^x[K][q] - omega_l D~^d[K][theta^l_w])
+// replaces D~^d in the scratch, its time-integral term accumulated in binary64 in It.
+template <int N, typename Real, bool CVT, bool HASX, int KC, int K>
+__device__ __forceinline__ Real ve_row(const VeTables<Real>& V, size_t tile, int w, int lane, int kk,
+                                       const Real* __restrict__ Xsh, const int (&scol)[3], int cnt, int s0,
+                                       const Real (&om)[3], Real dtr, double cw, double* __restrict__ It, Real v) {
+  constexpr int B = Dims<N>::B;
+  constexpr size_t LS = (size_t)6 * B * kTile;         // mechanism stride (theta scratch and I)
+  Real* th = V.theta + ((tile * kNTheta + w) * B + K) * kTile + lane;
+  double* ith = It + ((size_t)(9 + w) * B + K) * kTile + lane;
+  const Real t[3] = {th[0], th[LS], th[2 * LS]};
+  v -= (t[0] + t[1]) + t[2];                             // E_{sigma_i, theta^l_i} = -1
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    Real u = Real(0);
+    if constexpr (HASX) {
+      const Real* c = V.cth + (((tile * 3 + l) * 3) * kStressSlots + s0) * kTile + lane;
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+          if (s < cnt) u = fma(__ldg(c + (x * kStressSlots + s) * kTile), Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], u);
+    }
+    u = fma(-om[l], t[l], u);                            // E_{theta, theta} = -omega_l
+    u *= dtr;
+    th[l * LS] = u;
+    ith[l * LS] = fma(cw, to_f64<Real, CVT>(u), ith[l * LS]);
+  }
+  return v;
+}
+
 template <int N, int DELTA, typename Real, int RS, int S>
 __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, const int (&scol)[3], int cnt,
                                         Real* __restrict__ Dsh, Real (&D)[S], Real* __restrict__ Xsh,
@@ -293,6 +343,73 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
   }
 }
 
+// 27 quantities: every derivative runs the same unrestricted lists (those of delta = 0:
+// the source term keeps all B rows of D^delta non-zero), so the derivatives are a runtime
+// loop around one unrolled body (N times less code than unrolling them).  Each
+// derivative mixes all B rows: rows of degree < N as above; the stress warps add the
+// feedback -sum_l theta^l_i and advance their anelastic functions (ve_row); the stress
+// rows of degree N (only the feedback reaches them) accumulate their time integral in
+// the output array It itself; the velocity rows of degree N stay zero.  The operand
+// column D (registers, rows >= RS in shared memory) holds all B rows.
+template <int N, typename Real, int RS, int S>
+__device__ __forceinline__ void ck_ve(const StepTables<Real>& T, double dt, const int (&scol)[3], int cnt,
+                                      Real* __restrict__ Dsh, Real (&D)[S], Real* __restrict__ Xsh,
+                                      const Real (&sc)[3][3], double* __restrict__ Ish, int w, int lane,
+                                      const VeTables<Real>& V, size_t tile, int s0, const Real (&om)[3],
+                                      double* __restrict__ It) {
+  using Dm = Dims<N>;
+  constexpr int B = Dm::B, NI = Dm::nd(1);
+  constexpr int KC = LocalExchange<N, Real>::KCK;
+  constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
+  static_assert(RS > 0, "the time-integral accumulator is in shared memory");
+  const Real* xcol = Dsh + w * kTile + lane;
+  const Real dtr = (Real)dt;
+#pragma unroll 1
+  for (int delta = 0; delta < N; ++delta) {
+    const double cw = dt * T.invfact[delta + 1];
+    static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
+      constexpr int k0 = decltype(chunk)::value * KC;
+      if constexpr (k0 < NI) {
+        static_for<0, KC>([&](auto kkc) {
+          constexpr int kk = decltype(kkc)::value;
+          if constexpr (k0 + kk < NI) {
+            Xsh[((0 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 0, k0 + kk, RS>(T.val, D, xcol);
+            Xsh[((1 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 1, k0 + kk, RS>(T.val, D, xcol);
+            Xsh[((2 * KC + kk) * kNq + w) * kTile + lane] = row_op<N, 2, k0 + kk, RS>(T.val, D, xcol);
+          }
+        });
+        __syncthreads();
+      }
+      static_for<0, KC>([&](auto kkc) {
+        constexpr int kk = decltype(kkc)::value;
+        constexpr int k = k0 + kk;
+        if constexpr (k < B) {
+          Real v = Real(0);
+          if constexpr (k < NI) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+#pragma unroll
+              for (int s = 0; s < 3; ++s)
+                if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
+          }
+          if (w < 6) v = ve_row<N, Real, CVT, (k < NI), KC, k>(V, tile, w, lane, kk, Xsh, scol, cnt, s0, om, dtr, cw, It, v);
+          v *= dtr;
+          if constexpr (k < RS) D[k < RS ? k : 0] = v;
+          else Dsh[((k - RS) * kNq + w) * kTile + lane] = v;
+          if constexpr (k < NI) {
+            double* ip = Ish + (k * kNq + w) * kTile + lane;
+            *ip = fma(cw, to_f64<Real, CVT>(v), *ip);
+          } else if (w < 6) {
+            double* ip = It + ((size_t)w * B + k) * kTile + lane;
+            *ip = fma(cw, to_f64<Real, CVT>(v), *ip);
+          }
+        }
+      });
+      if constexpr (k0 < NI) __syncthreads();
+    });
+  }
+}
+
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume and local flux of one tile of 32 elements.
 //   Q, Qout : [tile][9][B][32] double   (may alias)
@@ -306,11 +423,16 @@ __device__ __forceinline__ void ck_step(const StepTables<Real>& T, double dt, co
 //                                       false (the full step lifts it together with the
 //                                       neighbour contribution in k_neigh)
 // LIFT = true applies the local flux here (Q is then the complete local update).
-template <int N, bool LIFT, typename Real>
+// VE: 27 quantities (Q, Qout, Iout are [tile][27][B][32]); the elastic rows as above
+// with the source terms, the anelastic functions' derivatives and time integral by the
+// stress warps (their volume, source and flux terms are k_theta's).
+template <int N, bool LIFT, typename Real, bool VE = false>
 __global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value))
 k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
-        const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs) {
+        const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs,
+        VeTables<Real> V) {
   using Dm = Dims<N>;
+  constexpr int NQT = VE ? kNqVe : kNq;      // quantities per element in Q and I
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
   constexpr int XR = LocalExchange<N, Real>::XR;
   constexpr bool ALIAS = LocalExchange<N, Real>::alias;
@@ -340,7 +462,8 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
     tile = (size_t)r.tile;
     dt = r.dt;
   }
-  const double* Qt = Q + tile * (kNq * B * kTile);
+  const double* Qt = Q + tile * (NQT * B * kTile);
+  double* It = Iout + tile * (NQT * B * kTile);
 
   // star coefficients of row p = w
   const int s0 = SP.start[w], cnt = SP.start[w + 1] - s0;
@@ -357,6 +480,27 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   constexpr int NI = Dm::nd(1);
   Real D[SD];           // operand rows < RS
   double Icol[NI];      // time-integral accumulator (RS == 0)
+  Real om[3] = {Real(0), Real(0), Real(0)};
+  if constexpr (VE) {
+    if (w < 6) {
+      // D~^0 of this warp's anelastic functions and their time-integral accumulators;
+      // the accumulators of the stress rows of degree N (fed by the source) in I itself
+      constexpr size_t LS = (size_t)6 * B * kTile;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) om[l] = __ldg(V.om + (tile * 3 + l) * kTile + lane);
+      Real* th = V.theta + ((tile * kNTheta + w) * B) * kTile + lane;
+      const double* qth = Qt + ((size_t)(9 + w) * B) * kTile + lane;
+      double* ith = It + ((size_t)(9 + w) * B) * kTile + lane;
+      for (int k = 0; k < B; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          const double q = qth[l * LS + k * kTile];
+          th[l * LS + k * kTile] = from_f64<Real, CVT>(q);
+          ith[l * LS + k * kTile] = dt * T.invfact[0] * q;
+        }
+      for (int k = NI; k < B; ++k) It[((size_t)w * B + k) * kTile + lane] = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+    }
+  }
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const double q = __ldg(Qt + (w * B + k) * kTile + lane);
@@ -370,14 +514,16 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   }
   // (own column only is read before the first barrier)
   const Real* xcol = Dsh + w * kTile + lane;      // this thread's shared operand rows
-  ck_step<N, 0, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Icol, Ish, w, lane);
+  if constexpr (VE) ck_ve<N, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Ish, w, lane, V, tile, s0, om, It);
+  else ck_step<N, 0, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Icol, Ish, w, lane);
 
   // publish I: operand column (own) and HBM
-  double* It = Iout + tile * (kNq * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     double ik;
-    if constexpr (RS > 0)
+    if (VE && w < 6 && k >= NI)
+      ik = It[(w * B + k) * kTile + lane];
+    else if constexpr (RS > 0)
       ik = k < NI ? Ish[(k * kNq + w) * kTile + lane] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
     else
       ik = k < NI ? Icol[k < NI ? k : 0] : dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
@@ -389,7 +535,7 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   // The volume term is added to each row of Q as soon as its chunk is done; with LIFT the
   // local flux is then added face by face (every row of an element column belongs to
   // one thread, so these read-modify-writes need no synchronisation).
-  double* Qo = Qout + tile * (kNq * B * kTile);
+  double* Qo = Qout + tile * (NQT * B * kTile);
   // exchange of the volume and flux phases: the accumulator rows when ALIAS (each thread
   // has read its own accumulator column above and writes only its own column before the
   // next barrier)
@@ -417,7 +563,14 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
 #pragma unroll
           for (int s = 0; s < 3; ++s)
             if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v);
+        double src = 0.0;                        // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
+        if constexpr (VE) {
+          if (w < 6) {
+            const double* ith = It + ((size_t)(9 + w) * B + k) * kTile + lane;
+            src = -((ith[0] + ith[(size_t)6 * B * kTile]) + ith[(size_t)12 * B * kTile]);
+          }
+        }
+        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v) + src;
       }
     });
     __syncthreads();
@@ -491,7 +644,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // so that Rhat^s is applied once per face to the sum of both flux contributions.
 // The four faces' W (BT x 9 each) stay in shared memory; every row k of Q is then
 // updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
-template <int N, bool WITH_LOCAL, typename Real>
+// NQT: quantities per element of Q (27 for the elastic rows of a 27-quantity step).
+template <int N, bool WITH_LOCAL, typename Real, int NQT = kNq>
 __global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, false>::value))
 k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
         StepTables<Real> T, const TileRef* __restrict__ refs) {
@@ -538,7 +692,7 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   // lifting of faces F0 .. F0 + NF - 1: every row k of Q gets the sum over these faces of
   // Rhat^s_k. W^s, summed in the contraction type (FP64: one chain), then one binary64
   // update (each thread reads only its own columns of Wsh)
-  double* Qt = Q + tile * (kNq * B * kTile);
+  double* Qt = Q + tile * (NQT * B * kTile);
   auto lift = [&](auto f0, auto nf) {
     constexpr int F0 = decltype(f0)::value, NF = decltype(nf)::value;
     const Real* wcol = Wsh + w * kTile + lane;
@@ -607,6 +761,165 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
     lift(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
 }
 
+// ------------------------------------------------------------------------- K_theta
+// The anelastic rows of a 27-quantity step (after k_local<N, false, Real, true>, beside
+// k_neigh<N, true, Real, 27>, which updates only the elastic rows): for each anelastic
+// function t = (l, i) of mechanism l and component i,
+//   Q[k][t] += sum_x sum_q Astar^x_tq (Khat^x I)[k][q] - omega_l I[k][t]      (volume, source)
+//            + sum_s Rhat^s_k. ((R^sT I) Aloc_s,t^T + f^h (R^jT I_nb) Anb_s,t^T) (fluxes)
+// The star rows of theta^l_i have the slots of stress row i (velocity columns only), so
+// the volume needs Khat^x I for the three velocity columns: warp w forms the three
+// directions of velocity column 6 + w % 3 for the rows k = w / 3 (mod 3).  The flux
+// terms need the face projections of this element and of its neighbours (written by
+// k_local): both are staged per face in shared memory, then every warp mixes them into
+// the flux products of its two anelastic functions t = w, w + 9 (registers) and lifts
+// them into Q (one binary64 update of the column per face).
+//   Q, I   : [tile][27][B][32] double
+//   Pown   : [element][4][9][BT]  R^sT I of the elastic quantities of this launch's tiles
+//   Pface  : the same for all elements (gathered by neighbour index)
+//   fthl, fthn : [tile][4][18][9][32] anelastic rows of the local / neighbour flux solvers
+template <int N, typename Real>
+__global__ void __launch_bounds__(kNq * kTile, 1)
+k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, const Real* __restrict__ Pface,
+        const int* __restrict__ conn, const Real* __restrict__ fthl, const Real* __restrict__ fthn,
+        StepTables<Real> T, StarPattern SP, VeTables<Real> V) {
+  using Dm = Dims<N>;
+  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
+  constexpr int RS = LocalRegRows<N, Real>::value;
+  constexpr int SD = RS > 0 ? RS : 1;
+  constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
+  constexpr size_t TQ = (size_t)kNqVe * B * kTile;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Dsh = reinterpret_cast<Real*>(smem_raw);            // operand rows >= RS: [B - RS][9][32]
+  Real* Xsh = Dsh + (B - RS) * kNq * kTile;                 // [KC][9][32] volume, then [2][BT][9][32]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t tile = blockIdx.x;
+  const size_t e = tile * kTile + lane;
+  double* Qt = Q + tile * TQ;
+  const double* It = I + tile * TQ;
+
+  // this warp's anelastic functions t = w, w + 9 -> (mechanism, component), star slots
+  int tl[2], ti[2], ts0[2], tcnt[2], tcol[2][3];
+  Real tom[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int t = w + 9 * c;
+    tl[c] = t / 6;
+    ti[c] = t % 6;
+    ts0[c] = SP.start[ti[c]];
+    tcnt[c] = SP.start[ti[c] + 1] - ts0[c];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) tcol[c][s] = (s < tcnt[c]) ? SP.col[ts0[c] + s] - 6 : 0;
+    tom[c] = __ldg(V.om + (tile * 3 + tl[c]) * kTile + lane);
+  }
+
+  // ---- volume and source
+  const int qv = 6 + w % 3, rc = w / 3;
+  Real D[SD];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const Real v = from_f64<Real, CVT>(It[(qv * B + k) * kTile + lane]);
+    if (k < RS) D[k < RS ? k : 0] = v;
+    else Dsh[((k - RS) * kNq + w) * kTile + lane] = v;
+  }
+  const Real* xcol = Dsh + w * kTile + lane;
+  static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
+    constexpr int k0 = decltype(chunk)::value * KC;
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      constexpr int k = k0 + kk;
+      if constexpr (k < B) {
+        if (k % 3 == rc) {
+          Xsh[(kk * kNq + 0 + (qv - 6)) * kTile + lane] = row_op<N, 18, k, RS>(T.val, D, xcol);
+          Xsh[(kk * kNq + 3 + (qv - 6)) * kTile + lane] = row_op<N, 19, k, RS>(T.val, D, xcol);
+          Xsh[(kk * kNq + 6 + (qv - 6)) * kTile + lane] = row_op<N, 20, k, RS>(T.val, D, xcol);
+        }
+      }
+    });
+    __syncthreads();
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      constexpr int k = k0 + kk;
+      if constexpr (k < B) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int t = w + 9 * c;
+          const Real* cc = V.cth + (((tile * 3 + tl[c]) * 3) * kStressSlots + ts0[c]) * kTile + lane;
+          Real u = Real(0);
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+              if (s < tcnt[c]) u = fma(__ldg(cc + (x * kStressSlots + s) * kTile), Xsh[(kk * kNq + 3 * x + tcol[c][s]) * kTile + lane], u);
+          const size_t o = ((size_t)(9 + t) * B + k) * kTile + lane;
+          Qt[o] += to_f64<Real, CVT>(u) - (double)tom[c] * It[o];
+        }
+      }
+    });
+    __syncthreads();
+  });
+
+  // ---- fluxes, face by face
+  Real* Yl = Xsh;                              // own projections   [BT][9][32]
+  Real* Yn = Xsh + BT * kNq * kTile;           // neighbour's, f^h applied
+  static_for<0, 4>([&](auto face) {
+    constexpr int sf = decltype(face)::value;
+    const Real* P = Pown + ((e * 4 + sf) * kNq + w) * BT;
+    const int cn = __ldg(conn + e * 4 + sf);
+    const size_t nb = (size_t)(cn >> 7);
+    const int j = (cn >> 2) & 3, h = cn & 3;
+    const Real* Pn = Pface + ((nb * 4 + j) * kNq + w) * BT;
+    Real pn[BT];
+#pragma unroll
+    for (int m = 0; m < BT; ++m) {
+      Yl[(m * kNq + w) * kTile + lane] = P[m];
+      pn[m] = Pn[m];
+    }
+    const Real* fh = T.f + (size_t)h * BT * BT;
+#pragma unroll
+    for (int d = 0; d <= N; ++d) {
+      const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
+#pragma unroll
+      for (int m = lo; m < hi; ++m) {
+        Real v = Real(0);
+#pragma unroll
+        for (int n = lo; n < hi; ++n) v = fma(__ldg(fh + m + n * BT), pn[n], v);
+        Yn[(m * kNq + w) * kTile + lane] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int t = w + 9 * c;
+      const Real* al = fthl + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
+      const Real* an = fthn + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
+      Real a[kNq], b[kNq];
+#pragma unroll
+      for (int q = 0; q < kNq; ++q) {
+        a[q] = __ldg(al + q * kTile);
+        b[q] = __ldg(an + q * kTile);
+      }
+      Real Wr[BT];
+#pragma unroll
+      for (int m = 0; m < BT; ++m) {
+        Real v = Real(0);
+#pragma unroll
+        for (int q = 0; q < kNq; ++q) {
+          v = fma(a[q], Yl[(m * kNq + q) * kTile + lane], v);
+          v = fma(b[q], Yn[(m * kNq + q) * kTile + lane], v);
+        }
+        Wr[m] = v;
+      }
+      double* qc = Qt + ((size_t)(9 + t) * B) * kTile + lane;
+      static_for<0, B>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        qc[k * kTile] += to_f64<Real, CVT>(row_dotr<N, 25 + sf, k, Real, BT>(T.val, Wr));
+      });
+    }
+    __syncthreads();
+  });
+}
+
 // ------------------------------------------------------------------ launch helpers
 // Buffers typed by the contraction type are passed untyped and cast by the per-degree,
 // per-precision launch functions.
@@ -621,6 +934,10 @@ struct AderLaunch {
   double dt;
   StarPattern SP;
   const TileRef* refs;     // null: one problem, grid = ntiles; else grid = ntiles entries
+  // 27-quantity steps
+  void* theta;
+  const void *cth, *om, *fthl, *fthn;
+  size_t smem_theta;
   cudaStream_t stream;
 };
 
@@ -678,10 +995,50 @@ void ader_launch(const AderLaunch& L) {
   if constexpr (LOCAL) {
     k_local<N, !FUSED, Real><<<grid, kNq * kTile, L.smem_local, L.stream>>>(
         L.Q, L.Q, L.I, static_cast<Real*>(L.Pface), static_cast<Real*>(L.Wloc),
-        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP, L.refs);
+        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP, L.refs, VeTables<Real>{});
   } else {
     k_neigh<N, FUSED, Real><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(
         L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T, L.refs);
+  }
+}
+
+// Kernels of a 27-quantity step: WHICH 0 = k_local (VE, fused step), 1 = k_neigh on the
+// elastic rows (fused step), 2 = k_theta.
+// Shared memory of k_theta: operand rows outside the registers (as LocalRegRows: FP64
+// keeps C(N+2,3) rows in registers from degree 5 on) and the two face buffers.
+inline size_t ader_theta_smem(int N, bool f32) {
+  const int B = (N + 1) * (N + 2) * (N + 3) / 6, BT = (N + 1) * (N + 2) / 2;
+  const int rs = (!f32 && N >= 5) ? (N + 2) * (N + 1) * N / 6 : B;
+  return (size_t)(f32 ? 4 : 8) * ((B - rs) + 2 * BT) * kNq * kTile;
+}
+template <int N, typename Real, int WHICH>
+void ader_set_attribute_ve(size_t smem) {
+  if constexpr (WHICH == 0)
+    cudaFuncSetAttribute(k_local<N, false, Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else if constexpr (WHICH == 1)
+    cudaFuncSetAttribute(k_neigh<N, true, Real, kNqVe>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else
+    cudaFuncSetAttribute(k_theta<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template <int N, typename Real, int WHICH>
+void ader_launch_ve(const AderLaunch& L) {
+  const unsigned grid = (unsigned)L.ntiles;
+  const StepTables<Real> T = step_tables<Real>(L);
+  VeTables<Real> V;
+  V.theta = static_cast<Real*>(L.theta);
+  V.cth = static_cast<const Real*>(L.cth);
+  V.om = static_cast<const Real*>(L.om);
+  if constexpr (WHICH == 0) {
+    k_local<N, false, Real, true><<<grid, kNq * kTile, L.smem_local, L.stream>>>(
+        L.Q, L.Q, L.I, static_cast<Real*>(L.Pface), static_cast<Real*>(L.Wloc),
+        static_cast<const Real*>(L.star), static_cast<const Real*>(L.floc), T, L.SP, nullptr, V);
+  } else if constexpr (WHICH == 1) {
+    k_neigh<N, true, Real, kNqVe><<<grid, kNq * kTile, L.smem_neigh, L.stream>>>(
+        L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T, nullptr);
+  } else {
+    k_theta<N, Real><<<grid, kNq * kTile, L.smem_theta, L.stream>>>(
+        L.Q, L.I, static_cast<const Real*>(L.Pface), static_cast<const Real*>(L.groups.base[0]), L.conn,
+        static_cast<const Real*>(L.fthl), static_cast<const Real*>(L.fthn), T, L.SP, V);
   }
 }
 
@@ -696,7 +1053,10 @@ void ader_launch(const AderLaunch& L) {
   YT_DECLARE_ADER_VARIANT(N, P, lf)    \
   YT_DECLARE_ADER_VARIANT(N, P, ll)    \
   YT_DECLARE_ADER_VARIANT(N, P, nf)    \
-  YT_DECLARE_ADER_VARIANT(N, P, np)
+  YT_DECLARE_ADER_VARIANT(N, P, np)    \
+  YT_DECLARE_ADER_VARIANT(N, P, vl)    \
+  YT_DECLARE_ADER_VARIANT(N, P, vn)    \
+  YT_DECLARE_ADER_VARIANT(N, P, vt)
 YT_DECLARE_ADER_UNIT(1, f64)
 YT_DECLARE_ADER_UNIT(2, f64)
 YT_DECLARE_ADER_UNIT(3, f64)

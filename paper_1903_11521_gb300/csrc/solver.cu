@@ -124,28 +124,135 @@ __global__ void k_setup(const double* __restrict__ material, const double* __res
   }
 }
 
-// canonical [e][q][k] <-> element-blocked [tile][q][k][lane]
+// Setup of the anelastic rows of a 27-quantity solver (FP64, one thread per element):
+//   star slots of theta^l_i:  sum_j (dxi_x/dx_j) omega_l A^j_{sigma_i, v}(Y^lambda_l, Y^mu_l)
+//                             in the slots of stress row i (velocity columns);
+//   omega_l;
+//   flux-solver rows: the 27 x 27 A_n = [[A_e, 0], [C, 0]] (C = its anelastic rows, velocity
+//   columns only) is diagonalisable with the spectrum of A_e plus zeros, so |A_n| is the
+//   same even polynomial alpha A_n^2 + beta A_n^4, whose anelastic rows are
+//   C (alpha A_e + beta A_e^3); Aloc / Anb rows = -(2|S|/|J|)(C +- C (alpha A_e + beta A_e^3))/2.
+// att: [e][l][omega, Y^lambda, Y^mu]; outputs [tile][...][32] as the kernels read them.
+__global__ void k_setup_theta(const double* __restrict__ material, const double* __restrict__ jac,
+                              const double* __restrict__ att, int64_t E, int64_t Epad,
+                              double* __restrict__ cth, double* __restrict__ om,
+                              double* __restrict__ fthl, double* __restrict__ fthn) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Epad) return;
+  const int64_t tile = e / kTile;
+  const int lane = (int)(e % kTile);
+  if (e >= E) {
+    for (int i = 0; i < 3 * 3 * kStressSlots; ++i) cth[(tile * 3 * 3 * kStressSlots + i) * kTile + lane] = 0.0;
+    for (int i = 0; i < 3; ++i) om[(tile * 3 + i) * kTile + lane] = 0.0;
+    for (int i = 0; i < 4 * kNTheta * kNq; ++i) {
+      fthl[(tile * 4 * kNTheta * kNq + i) * kTile + lane] = 0.0;
+      fthn[(tile * 4 * kNTheta * kNq + i) * kTile + lane] = 0.0;
+    }
+    return;
+  }
+  const double rho = material[e * 3 + 0], lam = material[e * 3 + 1], mu = material[e * 3 + 2];
+  double J[9];
+  for (int i = 0; i < 9; ++i) J[i] = jac[e * 9 + i];
+  auto Jm = [&](int i, int c) { return J[i + 3 * c]; };
+  const double det = Jm(0, 0) * (Jm(1, 1) * Jm(2, 2) - Jm(1, 2) * Jm(2, 1)) -
+                     Jm(0, 1) * (Jm(1, 0) * Jm(2, 2) - Jm(1, 2) * Jm(2, 0)) +
+                     Jm(0, 2) * (Jm(1, 0) * Jm(2, 1) - Jm(1, 1) * Jm(2, 0));
+  double G[3][3];
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < 3; ++j) {
+      const int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (d + 1) % 3, c1 = (d + 2) % 3;
+      G[d][j] = (Jm(r0, c0) * Jm(r1, c1) - Jm(r0, c1) * Jm(r1, c0)) / det;
+    }
+  const double val[4] = {-(lam + 2.0 * mu), -lam, -mu, -1.0 / rho};
+  double A[3][81];
+  for (int j = 0; j < 3; ++j) {
+    for (int i = 0; i < 81; ++i) A[j][i] = 0.0;
+    for (int t = 0; t < 8; ++t) A[j][c_jac[j][t].p * 9 + c_jac[j][t].q] = val[c_jac[j][t].kind];
+  }
+  // anelastic Jacobian rows: Ath[l][j][i][v] (stress component i, velocity v)
+  double Ath[3][3][6][3];
+  for (int l = 0; l < 3; ++l) {
+    const double w = att[(e * 3 + l) * 3 + 0], yl = att[(e * 3 + l) * 3 + 1], ym = att[(e * 3 + l) * 3 + 2];
+    const double vy[3] = {-(yl + 2.0 * ym), -yl, -ym};
+    om[(tile * 3 + l) * kTile + lane] = w;
+    for (int j = 0; j < 3; ++j) {
+      for (int i = 0; i < 6; ++i)
+        for (int v = 0; v < 3; ++v) Ath[l][j][i][v] = 0.0;
+      for (int t = 0; t < 8; ++t)
+        if (c_jac[j][t].p < 6) Ath[l][j][c_jac[j][t].p][c_jac[j][t].q - 6] = w * vy[c_jac[j][t].kind];
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int p = 0; p < 6; ++p)
+        for (int s = c_star.start[p]; s < c_star.start[p + 1]; ++s) {
+          const int v = c_star.col[s] - 6;
+          double x = 0.0;
+          for (int j = 0; j < 3; ++j) x = fma(G[d][j], Ath[l][j][p][v], x);
+          cth[(((tile * 3 + l) * 3 + d) * kStressSlots + s) * kTile + lane] = x;
+        }
+  }
+  const double cp = sqrt((lam + 2.0 * mu) / rho), cs = sqrt(mu / rho);
+  const double alpha = (cp * cp + cp * cs + cs * cs) / (cp * cs * (cp + cs));
+  const double beta = -1.0 / (cp * cs * (cp + cs));
+  const double V[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int s = 0; s < 4; ++s) {
+    double X[3][3];
+    for (int v = 0; v < 3; ++v)
+      for (int i = 0; i < 3; ++i) {
+        const double* r = V[c_face_verts[s][v]];
+        X[v][i] = Jm(i, 0) * r[0] + Jm(i, 1) * r[1] + Jm(i, 2) * r[2];
+      }
+    double u[3], t[3], c[3];
+    for (int i = 0; i < 3; ++i) { u[i] = X[1][i] - X[0][i]; t[i] = X[2][i] - X[0][i]; }
+    c[0] = u[1] * t[2] - u[2] * t[1];
+    c[1] = u[2] * t[0] - u[0] * t[2];
+    c[2] = u[0] * t[1] - u[1] * t[0];
+    const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double area = 0.5 * len;
+    double An[81], A2[81], A3[81], qa[81];
+    for (int i = 0; i < 81; ++i) An[i] = (c[0] * A[0][i] + c[1] * A[1][i] + c[2] * A[2][i]) / len;
+    mat9_mul(An, An, A2);
+    mat9_mul(An, A2, A3);
+    for (int i = 0; i < 81; ++i) qa[i] = alpha * An[i] + beta * A3[i];
+    const double scale = -(2.0 * area / det) * 0.5;
+    for (int l = 0; l < 3; ++l)
+      for (int i = 0; i < 6; ++i) {
+        double Cn[9];
+        for (int q = 0; q < 9; ++q) Cn[q] = 0.0;
+        for (int v = 0; v < 3; ++v)
+          Cn[6 + v] = (c[0] * Ath[l][0][i][v] + c[1] * Ath[l][1][i][v] + c[2] * Ath[l][2][i][v]) / len;
+        for (int q = 0; q < 9; ++q) {
+          double a = 0.0;
+          for (int r = 6; r < 9; ++r) a = fma(Cn[r], qa[r * 9 + q], a);
+          const size_t o = ((((size_t)tile * 4 + s) * kNTheta + 6 * l + i) * kNq + q) * kTile + lane;
+          fthl[o] = scale * (Cn[q] + a);
+          fthn[o] = scale * (Cn[q] - a);
+        }
+      }
+  }
+}
+
+// canonical [e][q][k] <-> element-blocked [tile][q][k][lane], P quantities per element
 __global__ void k_to_blocked(const double* __restrict__ in, double* __restrict__ out,
-                             int64_t E, int64_t Epad, int B) {
+                             int64_t E, int64_t Epad, int B, int P) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = Epad * kNq * B;
+  const int64_t total = Epad * P * B;
   if (i >= total) return;
   const int lane = (int)(i % kTile);
   const int64_t rest = i / kTile;
   const int k = (int)(rest % B);
-  const int q = (int)((rest / B) % kNq);
-  const int64_t tile = rest / ((int64_t)B * kNq);
+  const int q = (int)((rest / B) % P);
+  const int64_t tile = rest / ((int64_t)B * P);
   const int64_t e = tile * kTile + lane;
-  out[i] = e < E ? in[(e * kNq + q) * B + k] : 0.0;
+  out[i] = e < E ? in[(e * P + q) * B + k] : 0.0;
 }
 __global__ void k_from_blocked(const double* __restrict__ in, double* __restrict__ out,
-                               int64_t E, int B) {
+                               int64_t E, int B, int P) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= E * kNq * B) return;
+  if (i >= E * P * B) return;
   const int k = (int)(i % B);
-  const int q = (int)((i / B) % kNq);
-  const int64_t e = i / ((int64_t)B * kNq);
-  out[i] = in[(((e / kTile) * kNq + q) * B + k) * kTile + (e % kTile)];
+  const int q = (int)((i / B) % P);
+  const int64_t e = i / ((int64_t)B * P);
+  out[i] = in[(((e / kTile) * P + q) * B + k) * kTile + (e % kTile)];
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
@@ -213,6 +320,12 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.dt = s->dt;
   L.refs = nullptr;
   L.SP = kStar;
+  L.theta = s->theta;
+  L.cth = s->cth_r;
+  L.om = s->om_r;
+  L.fthl = s->fthl_r;
+  L.fthn = s->fthn_r;
+  L.smem_theta = s->smem_theta;
   L.stream = st;
   return L;
 }
@@ -257,6 +370,15 @@ void set_smem(yt_solver* s) {
   s->smem_neigh = ader_neigh_smem(N, s->prec != YT_F64);
   YT_REQUIRE(s->smem_local <= 227 * 1024 && s->smem_neigh <= 227 * 1024, YT_ERR_UNSUPPORTED,
              "order too high for this precision");
+  if (s->P == kNqVe) {
+    s->smem_theta = ader_theta_smem(N, s->prec != YT_F64);
+    YT_REQUIRE(s->smem_theta <= 227 * 1024, YT_ERR_UNSUPPORTED, "order too high for this precision");
+    YT_VARIANT_SWITCH(ader_set_attribute, vl, s->smem_local);
+    YT_VARIANT_SWITCH(ader_set_attribute, vn, s->smem_neigh);
+    YT_VARIANT_SWITCH(ader_set_attribute, vt, s->smem_theta);
+    cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
+    return;
+  }
   YT_VARIANT_SWITCH(ader_set_attribute, lf, s->smem_local);
   YT_VARIANT_SWITCH(ader_set_attribute, ll, s->smem_local);
   YT_VARIANT_SWITCH(ader_set_attribute, nf, s->smem_neigh);
@@ -297,8 +419,15 @@ AderLaunch chunk_args(const AderLaunch& F, const yt_solver* s, int64_t t0, int64
   AderLaunch L = F;
   const size_t rb = s->real_bytes;
   L.ntiles = nt;
-  L.Q += (size_t)t0 * kNq * s->B * kTile;
-  L.I += (size_t)t0 * kNq * s->B * kTile;
+  L.Q += (size_t)t0 * s->P * s->B * kTile;
+  L.I += (size_t)t0 * s->P * s->B * kTile;
+  if (s->P == kNqVe) {
+    L.theta = static_cast<unsigned char*>(L.theta) + (size_t)t0 * kNTheta * s->B * kTile * rb;
+    L.cth = static_cast<const unsigned char*>(L.cth) + (size_t)t0 * 3 * 3 * kStressSlots * kTile * rb;
+    L.om = static_cast<const unsigned char*>(L.om) + (size_t)t0 * 3 * kTile * rb;
+    L.fthl = static_cast<const unsigned char*>(L.fthl) + (size_t)t0 * 4 * kNTheta * kNq * kTile * rb;
+    L.fthn = static_cast<const unsigned char*>(L.fthn) + (size_t)t0 * 4 * kNTheta * kNq * kTile * rb;
+  }
   L.Pface = static_cast<unsigned char*>(L.Pface) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
   L.Wloc = static_cast<unsigned char*>(L.Wloc) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
   L.star = static_cast<const unsigned char*>(L.star) + (size_t)t0 * 3 * kStarSlots * kTile * rb;
@@ -319,8 +448,14 @@ void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
     return;
   }
   const AderLaunch L = launch_args(s, st);
-  if (fused) YT_VARIANT_SWITCH(ader_launch, lf, L);
-  else YT_VARIANT_SWITCH(ader_launch, ll, L);
+  if (s->P == kNqVe) {
+    YT_REQUIRE(fused, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
+    YT_VARIANT_SWITCH(ader_launch, vl, L);
+  } else if (fused) {
+    YT_VARIANT_SWITCH(ader_launch, lf, L);
+  } else {
+    YT_VARIANT_SWITCH(ader_launch, ll, L);
+  }
   cuda_check(cudaGetLastError(), "k_local launch");
 }
 void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
@@ -330,8 +465,15 @@ void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
     return;
   }
   const AderLaunch L = launch_args(s, st);
-  if (fused) YT_VARIANT_SWITCH(ader_launch, nf, L);
-  else YT_VARIANT_SWITCH(ader_launch, np, L);
+  if (s->P == kNqVe) {
+    YT_REQUIRE(fused, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
+    YT_VARIANT_SWITCH(ader_launch, vn, L);
+    YT_VARIANT_SWITCH(ader_launch, vt, L);
+  } else if (fused) {
+    YT_VARIANT_SWITCH(ader_launch, nf, L);
+  } else {
+    YT_VARIANT_SWITCH(ader_launch, np, L);
+  }
   cuda_check(cudaGetLastError(), "k_neigh launch");
 }
 
@@ -363,34 +505,57 @@ void build_tables(yt_solver* s) {
   // of star row p, 24 per matrix): assigned sum_p (6 cnt_p - 1) = 135, added 144 per row
   const double mix_assigned = 6.0 * kStarSlots - 9.0, mix_added = 6.0 * kStarSlots;
   double fl = 9.0 * B;                                     // I = c0 Q
+  int off_kt0[3] = {0, 0, 0}, off_kh[3] = {0, 0, 0};
   for (int delta = 0; delta < N; ++delta) {
     const int nin = nd(delta), nout = nd(delta + 1);
     for (int x = 0; x < 3; ++x) {
       const double* K = R.Ktilde.data() + (size_t)x * B * B;
       const int off = csr.add(nout, nin, [&](int r, int c) { return K[r + (size_t)c * B]; });
+      if (delta == 0) off_kt0[x] = off;
       fl += assigned(off, nout);                           // X^x = Ktilde^x D
     }
     fl += nout * (mix_assigned + 2.0 * 9);                 // D' = sum_x X^x A^xT; I += c D'
   }
+  double fkh = 0.0;
   for (int x = 0; x < 3; ++x) {
     const double* K = R.Khat.data() + (size_t)x * B * B;
-    const int off = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
-    fl += assigned(off, B);                                // X^x = Khat^x I
+    off_kh[x] = csr.add(B, B, [&](int r, int c) { return K[r + (size_t)c * B]; });
+    fkh += assigned(off_kh[x], B);                         // X^x = Khat^x I
   }
-  fl += B * mix_added;                                     // Q += sum_x X^x A^xT
-  double fn = 0.0, lift_total = 0.0;
+  fl += fkh + B * mix_added;                               // Q += sum_x X^x A^xT
+  double fn = 0.0, lift_total = 0.0, fproj = 0.0, ftheta_faces = 0.0;
   for (int f = 0; f < 4; ++f) {
     const double* Rs = R.R.data() + (size_t)f * B * BT;
     const double* Rh = R.Rhat.data() + (size_t)f * B * BT;
     const int off_rt = csr.add(BT, B, [&](int r, int c) { return Rs[c + (size_t)r * B]; });
     const int off_rh = csr.add(B, BT, [&](int r, int c) { return Rh[r + (size_t)c * B]; });
-    fl += assigned(off_rt, BT);                            // P = R^T I
-    fl += BT * 9.0 * 17.0;                                 // Wloc = P Aloc^T
+    fproj += assigned(off_rt, BT) + BT * 9.0 * 17.0;      // P = R^T I; Wloc = P Aloc^T
     const double lift = 9.0 * 2.0 * nnz_total(off_rh, B);  // Q += Rhat W (per face)
     lift_total += lift;
     double blocks = 0.0;                                   // V = f^h P_nb, block-diagonal
     for (int d = 0; d <= N; ++d) blocks += (d + 1.0) * (2.0 * (d + 1.0) - 1.0);
     fn += 9.0 * blocks + BT * 9.0 * 18.0 + lift;           // W = Wloc + V Anb^T; lifting
+    // anelastic rows (27 quantities, k_theta): V as above; W of 18 functions from the 9
+    // local and 9 neighbour projections (18 products each); their lifting
+    ftheta_faces += 9.0 * blocks + BT * 18.0 * 35.0 + 2.0 * lift;
+  }
+  fl += fproj;
+  if (s->P == kNqVe) {
+    // 27 quantities.  k_local: every derivative uses the unrestricted lists of delta = 0
+    // and writes all B rows: elastic rows of degree < N as above; per row the stress
+    // feedback -sum_l theta^l_i (3 per stress row), the stress rows of degree N (scaling,
+    // accumulation: 3); the anelastic functions: rows of degree < N mix 3 cnt_i products
+    // plus -omega theta (6 cnt_i + 1), scaling 1, accumulation 2; rows of degree N 4.
+    const int NI = nd(1);
+    double kt0 = 0.0;
+    for (int x = 0; x < 3; ++x) kt0 += assigned(off_kt0[x], NI);
+    const double per_deriv = kt0 + NI * (mix_assigned + 2.0 * 9) + B * 18.0 + (B - NI) * 6 * 3.0 +
+                             NI * 3.0 * (6.0 * 15 + 6 * (1.0 + 1.0 + 2.0)) + (B - NI) * 3.0 * 6 * 4.0;
+    // I = c0 Q (27 quantities); volume of the elastic rows and their source (3 per stress row)
+    fl = 27.0 * B + N * per_deriv + fkh + B * mix_added + B * 18.0 + fproj;
+    // k_theta: Khat^x on the three velocity columns; per row and anelastic function the
+    // mixing (6 cnt_i - 1), the source -omega I and the update (3); the faces as above
+    fn += fkh / 3.0 + B * 3.0 * (6.0 * 15 + 6 * 2.0) + ftheta_faces;
   }
   // yt_step runs k_local without the local lifting and k_neigh with the sum of both flux
   // products lifted once (the flops of the lifting are the same as lifting them one by
@@ -403,6 +568,15 @@ void build_tables(yt_solver* s) {
   const double qb = 8.0 * 9 * B, pb = rb * 4 * 9 * BT;
   s->bytes_local = 3 * qb + 2 * pb + rb * (3 * kStarSlots + 4 * 81);   // + Wloc written
   s->bytes_neigh = 2 * qb + 2 * pb + rb * 4 * 81 + 16.0;               // + Wloc read
+  if (s->P == kNqVe) {
+    // k_local: Q read (27 quantities), elastic rows of Q written, I written (27), the
+    // anelastic coefficients read; k_theta: anelastic rows of Q read and written, I of
+    // the velocities and anelastic functions read, own and neighbour projections, the
+    // anelastic rows of both flux solvers
+    const double qt = 8.0 * 18 * B;
+    s->bytes_local += 2 * qt + rb * (3 * 3 * kStressSlots + 3);
+    s->bytes_neigh += 2 * qt + 8.0 * 21 * B + 2 * pb + rb * (2 * 4 * kNTheta * kNq + 3 * 3 * kStressSlots + 3);
+  }
   if (csr.col.size() > 0x7fffffff) throw Error(YT_ERR_UNSUPPORTED, "tables too large");
   s->n_values = (int64_t)csr.val.size();
   s->d_val = dalloc<double>(csr.val.size());
@@ -434,10 +608,16 @@ void build_tables(yt_solver* s) {
     // variant's translation unit)
     if (N <= 5) {
       int rc = 0;
-      YT_VARIANT_SWITCH(rc |= ader_upload, lf, v32.data(), v32.size());
-      YT_VARIANT_SWITCH(rc |= ader_upload, ll, v32.data(), v32.size());
-      YT_VARIANT_SWITCH(rc |= ader_upload, nf, v32.data(), v32.size());
-      YT_VARIANT_SWITCH(rc |= ader_upload, np, v32.data(), v32.size());
+      if (s->P == kNqVe) {
+        YT_VARIANT_SWITCH(rc |= ader_upload, vl, v32.data(), v32.size());
+        YT_VARIANT_SWITCH(rc |= ader_upload, vn, v32.data(), v32.size());
+        YT_VARIANT_SWITCH(rc |= ader_upload, vt, v32.data(), v32.size());
+      } else {
+        YT_VARIANT_SWITCH(rc |= ader_upload, lf, v32.data(), v32.size());
+        YT_VARIANT_SWITCH(rc |= ader_upload, ll, v32.data(), v32.size());
+        YT_VARIANT_SWITCH(rc |= ader_upload, nf, v32.data(), v32.size());
+        YT_VARIANT_SWITCH(rc |= ader_upload, np, v32.data(), v32.size());
+      }
       YT_REQUIRE(rc == 0, YT_ERR_CUDA, "upload of constant values failed");
     }
     s->d_val32 = dalloc<float>(v32.size());
@@ -501,7 +681,16 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     YT_REQUIRE(mesh->n_elements < (int64_t(1) << 24), YT_ERR_UNSUPPORTED, "at most 2^24 elements");
     const bool nb = mesh->neighbours != nullptr;
     YT_REQUIRE(!nb || (mesh->faces && mesh->orient), YT_ERR_INVALID, "faces/orient required with neighbours");
+    YT_REQUIRE(scheme->quantities == 0 || scheme->quantities == kNq || scheme->quantities == kNqVe,
+               YT_ERR_INVALID, "quantities must be 9 or 27");
+    const bool ve = scheme->quantities == kNqVe;
+    YT_REQUIRE(!ve || mesh->attenuation, YT_ERR_INVALID, "27-quantity solvers need the attenuation parameters");
+    YT_REQUIRE(ve || !mesh->attenuation, YT_ERR_INVALID, "attenuation parameters given to a 9-quantity solver");
+    YT_REQUIRE(!ve || scheme->precision == YT_F64 || scheme->precision == YT_F32, YT_ERR_UNSUPPORTED,
+               "27-quantity solvers: YT_F64 or YT_F32");
+    YT_REQUIRE(!ve || nb, YT_ERR_INVALID, "27-quantity solvers need the face connectivity");
     auto s = std::make_unique<yt_solver>();
+    s->P = ve ? kNqVe : kNq;
     s->N = scheme->order - 1;
     s->B = n_basis(s->N);
     s->BT = n_face_basis(s->N);
@@ -530,9 +719,16 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
                "generated kernels do not match the reference matrices (rebuild the library)");
     set_smem(s.get());
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t nq = (size_t)s->Epad * kNq * s->B;
+    const size_t nq = (size_t)s->Epad * s->P * s->B;
     s->Q = dalloc<double>(nq);
     s->I = dalloc<double>(nq);
+    if (ve) {
+      s->theta = dalloc<unsigned char>((size_t)s->Epad * kNTheta * s->B * s->real_bytes);
+      s->cth = dalloc<double>((size_t)s->Epad * 3 * 3 * kStressSlots);
+      s->om = dalloc<double>((size_t)s->Epad * 3);
+      s->fthl = dalloc<double>((size_t)s->Epad * 4 * kNTheta * kNq);
+      s->fthn = dalloc<double>((size_t)s->Epad * 4 * kNTheta * kNq);
+    }
     // face projections: rows of BT values, padded to 8 in the tensor-core form
     const size_t pbytes = (size_t)s->Epad * 4 * kNq *
                           (s->prec == YT_BF16X3_F32ACC ? (size_t)tc::up8(s->BT) : (size_t)s->BT) * s->real_bytes;
@@ -549,12 +745,18 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     if (nb) cuda_check(cudaMemcpyAsync(s->conn, conn.data(), conn.size() * sizeof(int), cudaMemcpyHostToDevice, st), "copy conn");
     double* dmat = dalloc<double>((size_t)s->E * 3);
     double* djac = dalloc<double>((size_t)s->E * 9);
+    double* datt = ve ? dalloc<double>((size_t)s->E * 9) : nullptr;
     cudaError_t e1 = cudaMemcpyAsync(dmat, mesh->material, (size_t)s->E * 3 * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaError_t e2 = cudaMemcpyAsync(djac, mesh->jacobian, (size_t)s->E * 9 * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (ve && e2 == cudaSuccess)
+      e2 = cudaMemcpyAsync(datt, mesh->attenuation, (size_t)s->E * 9 * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaError_t e3 = cudaMemcpyToSymbolAsync(c_star, &kStar, sizeof(kStar), 0, cudaMemcpyHostToDevice, st);
     cudaError_t e4 = cudaMemcpyToSymbolAsync(c_face_verts, kFaceVerts, sizeof(kFaceVerts), 0, cudaMemcpyHostToDevice, st);
     if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) {
       k_setup<<<blocks_for(s->Epad, 128), 128, 0, st>>>(dmat, djac, s->E, s->Epad, s->star, s->floc, s->fnb);
+      if (ve)
+        k_setup_theta<<<blocks_for(s->Epad, 128), 128, 0, st>>>(dmat, djac, datt, s->E, s->Epad, s->cth, s->om,
+                                                                s->fthl, s->fthn);
       e1 = cudaGetLastError();
     }
     if (e1 == cudaSuccess) {
@@ -566,16 +768,32 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
         k_to_float<<<blocks_for(ns, 256), 256, 0, st>>>(s->star, static_cast<float*>(s->star_r), ns);
         k_to_float<<<blocks_for(nf, 256), 256, 0, st>>>(s->floc, static_cast<float*>(s->floc_r), nf);
         k_to_float<<<blocks_for(nf, 256), 256, 0, st>>>(s->fnb, static_cast<float*>(s->fnb_r), nf);
+        if (ve) {
+          const int64_t nc = s->Epad * 3 * 3 * kStressSlots, no = s->Epad * 3, nt = s->Epad * 4 * kNTheta * kNq;
+          s->cth_r = dalloc<float>((size_t)nc);
+          s->om_r = dalloc<float>((size_t)no);
+          s->fthl_r = dalloc<float>((size_t)nt);
+          s->fthn_r = dalloc<float>((size_t)nt);
+          k_to_float<<<blocks_for(nc, 256), 256, 0, st>>>(s->cth, static_cast<float*>(s->cth_r), nc);
+          k_to_float<<<blocks_for(no, 256), 256, 0, st>>>(s->om, static_cast<float*>(s->om_r), no);
+          k_to_float<<<blocks_for(nt, 256), 256, 0, st>>>(s->fthl, static_cast<float*>(s->fthl_r), nt);
+          k_to_float<<<blocks_for(nt, 256), 256, 0, st>>>(s->fthn, static_cast<float*>(s->fthn_r), nt);
+        }
         e1 = cudaGetLastError();
       } else {
         s->star_r = s->star;
         s->floc_r = s->floc;
         s->fnb_r = s->fnb;
+        s->cth_r = s->cth;
+        s->om_r = s->om;
+        s->fthl_r = s->fthl;
+        s->fthn_r = s->fthn;
       }
     }
     cudaError_t e5 = cudaStreamSynchronize(st);
     cudaFree(dmat);
     cudaFree(djac);
+    if (datt) cudaFree(datt);
     cuda_check(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : (e4 != cudaSuccess ? e4 : e5))),
                "solver setup");
     *out = s.release();
@@ -588,15 +806,15 @@ extern "C" yt_status yt_solver_set_dofs(yt_solver* s, const double* dofs, yt_mem
     YT_REQUIRE(s && dofs, YT_ERR_INVALID, "null argument");
     YT_REQUIRE(where == YT_MEM_HOST || where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t n = (size_t)s->E * kNq * s->B;
+    const size_t n = (size_t)s->E * s->P * s->B;
     const double* src = dofs;
     if (where == YT_MEM_HOST) {
-      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
       cuda_check(cudaMemcpyAsync(s->staging, dofs, n * sizeof(double), cudaMemcpyHostToDevice, st), "H2D dofs");
       src = s->staging;
     }
-    const int64_t total = s->Epad * kNq * s->B;
-    k_to_blocked<<<blocks_for(total, 256), 256, 0, st>>>(src, s->Q, s->E, s->Epad, s->B);
+    const int64_t total = s->Epad * s->P * s->B;
+    k_to_blocked<<<blocks_for(total, 256), 256, 0, st>>>(src, s->Q, s->E, s->Epad, s->B, s->P);
     cuda_check(cudaGetLastError(), "k_to_blocked");
   });
 }
@@ -608,14 +826,14 @@ extern "C" yt_status yt_solver_get(yt_solver* s, yt_field field, double* out, yt
     YT_REQUIRE(field == YT_FIELD_DOFS || field == YT_FIELD_TIME_INTEGRAL, YT_ERR_INVALID, "field");
     YT_REQUIRE(where == YT_MEM_HOST || where == YT_MEM_DEVICE, YT_ERR_INVALID, "where");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t n = (size_t)s->E * kNq * s->B;
+    const size_t n = (size_t)s->E * s->P * s->B;
     double* dst = out;
     if (where == YT_MEM_HOST) {
-      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
       dst = s->staging;
     }
     k_from_blocked<<<blocks_for((int64_t)n, 256), 256, 0, st>>>(field == YT_FIELD_DOFS ? s->Q : s->I,
-                                                                 dst, s->E, s->B);
+                                                                 dst, s->E, s->B, s->P);
     cuda_check(cudaGetLastError(), "k_from_blocked");
     if (where == YT_MEM_HOST)
       cuda_check(cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
@@ -625,6 +843,7 @@ extern "C" yt_status yt_solver_get(yt_solver* s, yt_field field, double* out, yt
 extern "C" yt_status yt_step_local(yt_solver* s, yt_stream stream) {
   return guarded([&] {
     YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(s->P == kNq, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
     dispatch_local(s, reinterpret_cast<cudaStream_t>(stream), false);
   });
 }
@@ -632,6 +851,7 @@ extern "C" yt_status yt_step_local(yt_solver* s, yt_stream stream) {
 extern "C" yt_status yt_step_neighbour(yt_solver* s, yt_stream stream) {
   return guarded([&] {
     YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(s->P == kNq, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
     YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
     dispatch_neigh(s, reinterpret_cast<cudaStream_t>(stream), false);
   });
@@ -668,8 +888,18 @@ void dispatch_chunk(yt_solver* s, cudaStream_t st, int phase, int64_t t0, int64_
     else tc_launch_neigh(s->N, T, 0);
   } else {
     const AderLaunch L = chunk_args(launch_args(s, st), s, t0, nt);
-    if (phase == 0) YT_VARIANT_SWITCH(ader_launch, lf, L);
-    else YT_VARIANT_SWITCH(ader_launch, nf, L);
+    if (s->P == kNqVe) {
+      if (phase == 0) {
+        YT_VARIANT_SWITCH(ader_launch, vl, L);
+      } else {
+        YT_VARIANT_SWITCH(ader_launch, vn, L);
+        YT_VARIANT_SWITCH(ader_launch, vt, L);
+      }
+    } else if (phase == 0) {
+      YT_VARIANT_SWITCH(ader_launch, lf, L);
+    } else {
+      YT_VARIANT_SWITCH(ader_launch, nf, L);
+    }
   }
   cuda_check(cudaGetLastError(), "chunk launch");
 }
@@ -682,7 +912,7 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
     YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     constexpr int kChunks = 8;
-    if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * kNq * s->B);
+    if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
     if (!s->copy_stream) {
       cuda_check(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "copy stream");
       cuda_check(cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming), "event");
@@ -694,7 +924,7 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
     }
     cudaStream_t cp = s->copy_stream;
     const int64_t per = (s->ntiles + kChunks - 1) / kChunks;     // tiles per chunk
-    const size_t row = (size_t)kNq * s->B;                       // doubles per element
+    const size_t row = (size_t)s->P * s->B;                      // doubles per element
     cuda_check(cudaEventRecord(s->ev_start, st), "event record");
     cuda_check(cudaStreamWaitEvent(cp, s->ev_start, 0), "stream wait");
     // uploads on the copy stream; layout conversion and local kernel per chunk on `st`
@@ -708,7 +938,7 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
       cuda_check(cudaStreamWaitEvent(st, s->ev_in[c], 0), "stream wait");
       const int64_t total = nt * kTile * (int64_t)row;
       k_to_blocked<<<blocks_for(total, 256), 256, 0, st>>>(s->staging + e0 * row, s->Q + e0 * row, ne,
-                                                           nt * kTile, s->B);
+                                                           nt * kTile, s->B, s->P);
       cuda_check(cudaGetLastError(), "k_to_blocked");
       dispatch_chunk(s, st, 0, t0, nt);
     }
@@ -719,7 +949,7 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
       const int64_t e0 = t0 * kTile, ne = std::min<int64_t>(nt * kTile, s->E - e0);
       dispatch_chunk(s, st, 1, t0, nt);
       k_from_blocked<<<blocks_for(ne * (int64_t)row, 256), 256, 0, st>>>(s->Q + e0 * row,
-                                                                         s->staging + e0 * row, ne, s->B);
+                                                                         s->staging + e0 * row, ne, s->B, s->P);
       cuda_check(cudaGetLastError(), "k_from_blocked");
       cuda_check(cudaEventRecord(s->ev_out[c], st), "event record");
       cuda_check(cudaStreamWaitEvent(cp, s->ev_out[c], 0), "stream wait");
@@ -923,6 +1153,8 @@ extern "C" yt_status yt_batch_create(const yt_mesh_desc* mesh, const int8_t* ord
     YT_REQUIRE(mesh->n_elements > 1 && mesh->n_elements < (int64_t(1) << 24), YT_ERR_INVALID,
                "element count must be 2 .. 2^24-1");
     YT_REQUIRE(scheme->flags == 0, YT_ERR_INVALID, "scheme flags must be 0");
+    YT_REQUIRE((scheme->quantities == 0 || scheme->quantities == kNq) && !mesh->attenuation,
+               YT_ERR_UNSUPPORTED, "p-adaptive batches: 9 quantities");
     auto b = std::make_unique<yt_batch>();
     b->prec = scheme->precision;
     b->dt = scheme->dt;

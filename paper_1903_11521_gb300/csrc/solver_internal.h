@@ -9,6 +9,7 @@
 
 struct yt_solver {
   int N = 0, B = 0, BT = 0;
+  int P = 9;                          // quantities: 9 elastic, 27 viscoelastic-shaped
   int64_t E = 0, Epad = 0, ntiles = 0;
   yt_precision prec = YT_F64;
   double dt = 0.0;
@@ -35,12 +36,21 @@ struct yt_solver {
   int* d_status = nullptr;
   unsigned tc_grid = 0;
   bool diag_expire_wait = false;     // YT_SCHEME_DIAG_EXPIRE_WAIT
+  // 27 quantities: anelastic star slots, relaxation frequencies and flux-solver rows (FP64
+  // setup copies and the contraction type's), the derivative scratch of the anelastic
+  // functions, shared memory of k_theta
+  double *cth = nullptr, *om = nullptr, *fthl = nullptr, *fthn = nullptr;
+  void *cth_r = nullptr, *om_r = nullptr, *fthl_r = nullptr, *fthn_r = nullptr, *theta = nullptr;
+  size_t smem_theta = 0;
   // yt_step_host: copy stream and per-chunk events (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   cudaEvent_t ev_in[16] = {}, ev_out[16] = {};
   ~yt_solver() {
     if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
+    if (cth_r == (void*)cth) cth_r = om_r = fthl_r = fthn_r = nullptr;
+    for (void* p : {(void*)cth, (void*)om, (void*)fthl, (void*)fthn, cth_r, om_r, fthl_r, fthn_r, theta})
+      if (p) cudaFree(p);
     for (cudaEvent_t e : ev_in) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_out) if (e) cudaEventDestroy(e);
     if (ev_start) cudaEventDestroy(ev_start);

@@ -28,7 +28,9 @@ class Solver:
     or None.  DOFs are exchanged in the canonical layout [element][quantity][basis]."""
 
     def __init__(self, order, dt, material, jacobian, neighbours=None, faces=None,
-                 orient=None, precision=_lib.YT_F64, stream=None, flags=0):
+                 orient=None, precision=_lib.YT_F64, stream=None, flags=0, attenuation=None):
+        """attenuation: None (elastic, 9 quantities) or an object with (E, 3) arrays
+        omega, ylam, ymu of the three mechanisms (27 quantities)."""
         self.lib = _lib.load()
         E = int(np.asarray(material).shape[0])
         self.n_elements = E
@@ -48,7 +50,15 @@ class Solver:
             desc.neighbours = _ptr(self._nb, C.c_int32)
             desc.faces = _ptr(self._fj, C.c_int8)
             desc.orient = _ptr(self._fh, C.c_int8)
-        sch = _lib.SchemeDesc(order=self.order, dt=float(dt), precision=precision, flags=int(flags))
+        self.n_quantities = 9
+        if attenuation is not None:
+            self._att = np.ascontiguousarray(np.stack([attenuation.omega, attenuation.ylam,
+                                                       attenuation.ymu], axis=2), dtype=np.float64)
+            assert self._att.shape == (E, 3, 3)
+            desc.attenuation = _ptr(self._att, C.c_double)
+            self.n_quantities = 27
+        sch = _lib.SchemeDesc(order=self.order, dt=float(dt), precision=precision, flags=int(flags),
+                              quantities=self.n_quantities)
         handle = C.c_void_p()
         _lib.check(self.lib.yt_solver_create(C.byref(desc), C.byref(sch),
                                              _stream_handle(stream), C.byref(handle)),
@@ -69,7 +79,7 @@ class Solver:
 
     # ------------------------------------------------------------------ data movement
     def set_dofs_host(self, Q, stream=None):
-        """Q as numpy (E, B, 9) [element, basis, quantity] (the oracle's layout)."""
+        """Q as numpy (E, B, P) [element, basis, quantity] (the oracle's layout)."""
         canon = np.ascontiguousarray(np.asarray(Q, dtype=np.float64).transpose(0, 2, 1))
         self._host_in = canon
         _lib.check(self.lib.yt_solver_set_dofs(self.handle, canon.ctypes.data, _lib.YT_MEM_HOST,
@@ -84,8 +94,8 @@ class Solver:
                    "yt_solver_get")
 
     def get_host(self, field=_lib.YT_FIELD_DOFS, stream=None, sync=True):
-        """Field as numpy (E, B, 9); synchronises the device when sync is True."""
-        out = np.empty((self.n_elements, 9, self.n_basis))
+        """Field as numpy (E, B, P); synchronises the device when sync is True."""
+        out = np.empty((self.n_elements, self.n_quantities, self.n_basis))
         _lib.check(self.lib.yt_solver_get(self.handle, field, out.ctypes.data, _lib.YT_MEM_HOST,
                                           _stream_handle(stream)), "yt_solver_get")
         if sync:
