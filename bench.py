@@ -80,9 +80,11 @@ def parse():
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16x3"],
                     help="contraction type of the main measurement (default FP64)")
     ap.add_argument("--form", default=None,
-                    choices=["executor", "structured", "serving", "local_update"],
+                    choices=["executor", "structured", "viscoelastic", "serving", "local_update"],
                     help="run only this form of the forms section and print it as one JSON line "
                          "(for profiling one form)")
+    ap.add_argument("--form-steps", type=int, default=10,
+                    help="steps of the 27-quantity form at full size (--form viscoelastic)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batching and serving measurements")
     return ap.parse_args()
@@ -340,6 +342,25 @@ def form_structured(yt, stream, n=55, steps=100):
             acc += np.einsum('ebq,ebq->q', d, d)
         return acc
 
+    det = np.abs(np.linalg.det(el.jac))
+
+    def energy(q, order, chunk=65536):
+        # elastic energy 1/2 int (rho |v|^2 + sigma : S sigma) of the discrete solution:
+        # the mass matrix of the basis is diagonal, so per element
+        # 1/2 |J| sum_k M_kk (rho |v_k|^2 + sigma_k : S sigma_k), S the isotropic compliance
+        # sigma : S sigma = (sigma : sigma - lambda / (3 lambda + 2 mu) tr(sigma)^2) / (2 mu)
+        B = order * (order + 1) * (order + 2) // 6
+        Mk = np.diag(yt.reference_matrix(order, "M").reshape(B, B))
+        tot = 0.0
+        for i in range(0, E, chunk):
+            d = q[i:i + chunk]
+            rho, lam, mu = el.rho[i:i + chunk, None], el.lam[i:i + chunk, None], el.mu[i:i + chunk, None]
+            ss = (d[..., 0:3] ** 2).sum(-1) + 2.0 * (d[..., 3:6] ** 2).sum(-1)
+            tr = d[..., 0:3].sum(-1)
+            dens = rho * (d[..., 6:9] ** 2).sum(-1) + (ss - lam / (3 * lam + 2 * mu) * tr ** 2) / (2 * mu)
+            tot += 0.5 * float((det[i:i + chunk, None] * Mk[None, :] * dens).sum())
+        return tot
+
     def compare(order, forms):
         B = order * (order + 1) * (order + 2) // 6
         Q0 = wl.random_dofs(E, B, seed=wl.SEED + 800 + order, scale="impedance", elements=el)
@@ -348,13 +369,15 @@ def form_structured(yt, stream, n=55, steps=100):
         norm = np.sqrt(sq_per_quantity(q64).sum())
         res = {"fp64": {"value": E / (ms64 / 1e3), "unit": METRIC, "ms_per_step": ms64,
                         "finite": bool(np.isfinite(norm)),
+                        "energy_ratio": energy(q64, order) / energy(Q0, order),
                         "coefficient_norm_ratio": float(norm / np.sqrt(sq_per_quantity(Q0).sum()))}}
         for name, prec in forms:
             ms, q = run(order, prec, Q0, 0)
             per_q = np.sqrt(sq_per_quantity(q, q64))
             res[name] = {"value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms,
                          "error_vs_fp64_rel_solution": float(per_q.max() / norm),
-                         "error_vs_fp64_rel_change": float(per_q.max() / change)}
+                         "error_vs_fp64_rel_change": float(per_q.max() / change),
+                         "energy_ratio": energy(q, order) / energy(Q0, order)}
             del q
         return res
 
@@ -362,8 +385,109 @@ def form_structured(yt, stream, n=55, steps=100):
     out["order6"] = compare(6, (("fp32", yt.YT_F32), ("bf16x3", yt.YT_BF16X3_F32ACC)))
     out["error_definition"] = ("after 100 steps from the same DOFs: max over quantities of "
                                "||Q - Q_fp64||_F, divided by ||Q_fp64||_F (rel_solution) or by "
-                               "||Q_fp64 - Q_0||_F (rel_change)")
+                               "||Q_fp64 - Q_0||_F (rel_change); energy_ratio = elastic energy "
+                               "1/2 int(rho |v|^2 + sigma : S sigma) after the steps / before "
+                               "(mass-weighted; below 1: the upwind flux dissipates)")
     return out
+
+
+def form_viscoelastic(yt, stream, n=55, order=7, steps=10, n_long=20, steps_long=100):
+    """The 27-quantity precision form: order 7, the jittered periodic structured mesh of
+    n^3 x 6 tets (n = 55: 998,250), homogeneous elastic material, synthetic attenuation of
+    three mechanisms per element (workload.attenuation), N(0,1) DOFs scaled by impedance
+    (stresses) and impedance x omega (anelastic functions); FP64 and FP32 contractions,
+    `steps` steps each from the same DOFs (no warm-up: both take the same steps), the FP32
+    result after them against the FP64 path (which equals the oracle to 1e-15 per step,
+    tests/test_gpu_viscoelastic.py).  The error after `steps_long` steps is measured the same
+    way on the n_long^3 x 6 mesh of the same family (100 FP64 steps at full size take
+    two minutes)."""
+    out = _viscoelastic_run(yt, stream, n, order, steps)
+    if steps_long:
+        long = _viscoelastic_run(yt, stream, n_long, order, steps_long)
+        out["error_after_100_steps"] = {
+            "workload": long["workload"],
+            "error_vs_fp64_rel_solution": long["fp32"]["error_vs_fp64_rel_solution"],
+            "error_vs_fp64_rel_change": long["fp32"]["error_vs_fp64_rel_change"],
+            "error_vs_fp64_rel_solution_elastic": long["fp32"]["error_vs_fp64_rel_solution_elastic"],
+            "error_vs_fp64_rel_solution_anelastic": long["fp32"]["error_vs_fp64_rel_solution_anelastic"],
+            "fp64_finite": long["fp64"]["finite"]}
+    return out
+
+
+def _viscoelastic_run(yt, stream, n, order, steps):
+    mesh = wl.jittered_periodic_mesh(n, jitter=0.1, seed=wl.SEED + 800, length=100.0 * n,
+                                     rho=2500.0, lam=2.5e10, mu=2.5e10)
+    el, conn = mesh.elements, mesh.conn
+    E = el.rho.size
+    N = order - 1
+    B = order * (order + 1) * (order + 2) // 6
+    dt = wl.cfl_time_step(el, N)
+    att = wl.attenuation(el, dt, seed=wl.SEED + 900)
+    Q0 = wl.random_dofs_viscoelastic(E, B, el, att, seed=wl.SEED + 901)
+    mat = np.stack([el.rho, el.lam, el.mu], 1)
+
+    # full steps (phase 0, then phase 1), both phases timed with CUDA events
+    def run_steps(prec):
+        import torch
+        s = yt.Solver(order, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient,
+                      precision=prec, stream=stream, attenuation=att)
+        s.set_dofs_host(Q0, stream=stream)
+        st = s.stats()
+        evs = [[torch_event() for _ in range(3)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            evs[k][0].record(stream)
+            s.step_phase(0, stream=stream)
+            evs[k][1].record(stream)
+            s.step_phase(1, stream=stream)
+            evs[k][2].record(stream)
+        torch.cuda.synchronize()
+        total = evs[0][0].elapsed_time(evs[-1][2]) / steps
+        loc = sum(e[0].elapsed_time(e[1]) for e in evs) / steps
+        nei = sum(e[1].elapsed_time(e[2]) for e in evs) / steps
+        q = s.get_host(stream=stream)
+        s.close()
+        return q, st, total, loc, nei
+
+    def sq(a, b=None, chunk=32768):
+        acc = np.zeros(a.shape[-1])
+        for i in range(0, a.shape[0], chunk):
+            d = a[i:i + chunk] if b is None else a[i:i + chunk] - b[i:i + chunk]
+            acc += np.einsum('ebq,ebq->q', d, d)
+        return acc
+
+    out = {"workload": f"viscoelastic-shaped (3 mechanisms, 27 quantities), order {order} "
+                       f"(B={B}), jittered periodic structured mesh {n}^3 x 6 = {E} tets, "
+                       f"{steps} steps", "elements": E, "quantities": 27, "steps": steps}
+    q64, st64, t64, l64, n64 = run_steps(yt.YT_F64)
+    norm = np.sqrt(sq(q64))
+    change = np.sqrt(sq(q64, Q0))
+    out["fp64"] = {"value": E / (t64 / 1e3), "unit": METRIC, "ms_per_step": t64,
+                   "kernel_ms": {"k_local": l64, "k_neigh+k_theta": n64},
+                   "tflops": (st64["local_flops"] + st64["neighbour_flops"]) * E / (t64 / 1e3) / 1e12,
+                   "frac_fp64_peak": (st64["local_flops"] + st64["neighbour_flops"]) * E / (t64 / 1e3) / 1e12
+                   / FP64_PEAK_TFLOPS,
+                   "finite": bool(np.isfinite(norm).all())}
+    q32, st32, t32, l32, n32 = run_steps(yt.YT_F32)
+    per_q = np.sqrt(sq(q32, q64))
+    out["fp32"] = {"value": E / (t32 / 1e3), "unit": METRIC, "ms_per_step": t32,
+                   "kernel_ms": {"k_local": l32, "k_neigh+k_theta": n32},
+                   "tflops": (st32["local_flops"] + st32["neighbour_flops"]) * E / (t32 / 1e3) / 1e12,
+                   "error_vs_fp64_rel_solution": float((per_q / norm).max()),
+                   "error_vs_fp64_rel_change": float((per_q / change).max()),
+                   "error_vs_fp64_rel_solution_elastic": float((per_q[:9] / norm[:9]).max()),
+                   "error_vs_fp64_rel_solution_anelastic": float((per_q[9:] / norm[9:]).max())}
+    out["flops_per_element"] = {"local": st64["local_flops"], "neighbour_and_theta": st64["neighbour_flops"]}
+    out["error_definition"] = (f"after {steps} steps from the same DOFs: max over the 27 quantities "
+                               "of ||Q - Q_fp64||_F / ||Q_fp64||_F (rel_solution, the same restricted to "
+                               "the 9 elastic and the 18 anelastic quantities) or / ||Q_fp64 - Q_0||_F "
+                               "(rel_change)")
+    return out
+
+
+def torch_event():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
 
 
 def form_executor(yt, stream, order=6, E=200_000, S=8, reps=5):
@@ -558,6 +682,7 @@ def run_ours(args):
         stream = torch.cuda.current_stream()
         run = {"executor": lambda: form_executor(yt, stream),
                "structured": lambda: form_structured(yt, stream),
+               "viscoelastic": lambda: form_viscoelastic(yt, stream, steps=args.form_steps),
                "serving": lambda: form_serving(yt),
                "local_update": lambda: form_local_update(yt, 4, 1000, 200, stream)}[args.form]
         print(json.dumps({"form": args.form, "result": run()}), flush=True)
@@ -635,9 +760,28 @@ def run_ours(args):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e_ms = float(tt.item())
         nbytes = E * 9 * B * 8
+        # the copies alone (one each way, pinned host <-> device, on the same stream)
+        dev = torch.empty(canon.shape, dtype=canon.dtype, device="cuda")
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        c0.record(stream)
+        dev.copy_(canon, non_blocking=True)
+        c1.record(stream)
+        out.copy_(dev, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms = c0.elapsed_time(c1), c1.elapsed_time(c2)
+        del dev
+        seq_ms = h2d_ms + total_ms / K + d2h_ms
         e2e = {"value": ws * E * K / (e_ms / 1e3), "unit": METRIC,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": e_ms / K}
+               "ms_per_step": e_ms / K,
+               "h2d_gbs": nbytes / (h2d_ms / 1e3) / 1e9, "d2h_gbs": nbytes / (d2h_ms / 1e3) / 1e9,
+               "copy_ms_alone": [h2d_ms, d2h_ms],
+               "sequential_ms": seq_ms,
+               "overlap_fraction": max(0.0, min(1.0, (seq_ms - e_ms / K) / (h2d_ms + d2h_ms))),
+               "overlap_definition": "(H2D + device step + D2H, each alone) - e2e step, over the "
+                                     "copy time: the share of the copies hidden under the kernels"}
     solver.close()
 
     if rank != 0:
@@ -680,6 +824,7 @@ def run_ours(args):
                  "precision_o6_bf16x3": form_precision(yt, 6, E, 5, stream, "bf16x3"),
                  "precision_o7": form_precision(yt, 7, E, 5, stream),
                  "structured_mesh_100_steps": form_structured(yt, stream),
+                 "viscoelastic_o7": form_viscoelastic(yt, stream),
                  "executor": form_executor(yt, stream),
                  "batching_fp32": form_batching(yt, 2 * E, yt.YT_F32, 3, 7, 5, stream),
                  "batching_fp64": form_batching(yt, 2 * E, yt.YT_F64, 3, 7, 3, stream),
@@ -724,7 +869,8 @@ def run_reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args),
+            "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
+            "sample_elements": n,
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": workers, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
