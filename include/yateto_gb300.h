@@ -276,8 +276,7 @@ void yt_solver_destroy(struct yt_solver* solver);
  * volume and local flux; across a face, the neighbour's face projection is truncated or
  * zero-padded to the element's face basis (the hierarchical orthogonal basis makes this
  * the L2 projection).  The elements are grouped by degree; one step is one launch of a
- * CUDA graph recorded at creation (local kernels of every group, then neighbour kernels
- * of every group).  DOFs are exchanged in the packed canonical layout: element after
+ * CUDA graph recorded at creation (see the forms below).  DOFs are exchanged in the packed canonical layout: element after
  * element (in mesh order), each [quantity][basis] with its own B_e = C(o_e + 2, 3). */
 struct yt_batch;
 yt_status yt_batch_create(const yt_mesh_desc* mesh, const int8_t* orders /* host, E */,
@@ -288,11 +287,29 @@ yt_status yt_batch_set_dofs(struct yt_batch* batch, const double* dofs, yt_memor
 yt_status yt_batch_get(struct yt_batch* batch, yt_field field, double* out, yt_memory where,
                        yt_stream stream);
 yt_status yt_batch_step(struct yt_batch* batch, yt_stream stream);
-/* Autotuner: records the step both with the groups in sequence and with the groups on
- * parallel graph branches, replays each `repeats` times on the current data (the DOFs
- * are restored afterwards), keeps the faster graph and reports it in *chosen (0
- * sequential, 1 parallel). Synchronises `stream`. */
+/* Forms of the step (each recorded as one CUDA graph, one graph launch per step):
+ *   0: the per-degree local kernels in sequence, then the neighbour kernels;
+ *   1: the same kernels on parallel graph branches (one branch per degree);
+ *   2: one persistent kernel: a cooperative launch of one CTA per SM (as many as the
+ *      occupancy query allows) in which every CTA claims work items (degree group, tile)
+ *      from an atomic counter, `chunk` tiles per claim, in one of two orders (0: groups by
+ *      decreasing degree, the longest tiles first; 1: groups interleaved tile by tile);
+ *      the local phase of every group, then a grid-wide barrier (bounded wait, one
+ *      second, then YT_ERR_TIMEOUT through yt_batch_status), then the neighbour phase.
+ * A new batch uses form 0.  yt_batch_set_form selects a form (order and chunk apply to
+ * form 2). */
+yt_status yt_batch_set_form(struct yt_batch* batch, int32_t form, int32_t order, int32_t chunk);
+/* Autotuner: records every form (0, 1, and 2 with each order and chunk 1, 2, 4), replays
+ * each `repeats` times on the current data (the DOFs are restored afterwards), keeps the
+ * fastest and reports its form in *chosen.  Synchronises `stream`. */
 yt_status yt_batch_tune(struct yt_batch* batch, int32_t repeats, yt_stream stream, int32_t* chosen);
+/* Description of the form in use (and the tuner's timings after yt_batch_tune), as a
+ * NUL-terminated string of at most capacity - 1 characters. */
+yt_status yt_batch_config(const struct yt_batch* batch, char* out, int32_t capacity);
+/* Synchronises `stream`, then reports whether the persistent kernel's grid barrier ran
+ * out since the last call (YT_ERR_TIMEOUT, record cleared), else YT_OK.  No counterpart
+ * in the paper: a safeguard of this implementation. */
+yt_status yt_batch_status(struct yt_batch* batch, yt_stream stream);
 /* Flops and algorithmic device bytes of one step of the whole batch; number of groups. */
 yt_status yt_batch_stats(const struct yt_batch* batch, double* flops, double* bytes,
                          int32_t* n_groups);

@@ -83,6 +83,9 @@ SIGNATURES = {
     "yt_batch_get": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),
     "yt_batch_step": (C.c_int, [_P, _P]),
     "yt_batch_tune": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_int32)]),
+    "yt_batch_set_form": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "yt_batch_config": (C.c_int, [_P, C.c_char_p, C.c_int32]),
+    "yt_batch_status": (C.c_int, [_P, _P]),
     "yt_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "yt_batch_destroy": (None, [_P]),
     "yt_server_create": (C.c_int, [C.POINTER(ServerDesc), C.POINTER(_P)]),

@@ -98,8 +98,11 @@ def emit_rows(N, lst, nvals):
     lines = []
     if N <= CONST_MAX_N:
         # FP32 values in constant memory: each non-zero becomes one fma with a
-        # constant-bank operand (one copy per translation unit, uploaded by the solver)
+        # constant-bank operand (one copy per translation unit, uploaded by the solver);
+        # not in the batch kernel's units (YT_ROWS_GLOBAL)
+        lines.append("#ifndef YT_ROWS_GLOBAL")
         lines.append(f"static __constant__ float c_vals_o{N}[{max(nvals, 1)}];")
+        lines.append("#endif")
     for list_id, rows in lst:
         for r, row in enumerate(rows):
             lines.append(f"template <> struct Row<{N}, {list_id}, {r}> {{")
@@ -148,6 +151,7 @@ def emit_rows(N, lst, nvals):
             lines.append("    return a;")
             lines.append("  }")
             if N <= CONST_MAX_N:
+                lines.append("#ifndef YT_ROWS_GLOBAL")
                 lines.append("  template <int S>")
                 lines.append("  static __device__ __forceinline__ float dotrc(const float (&x)[S]) {")
                 if not row:
@@ -182,6 +186,7 @@ def emit_rows(N, lst, nvals):
                                  for i in range(0, len(terms), 2)]
                     lines.append(f"    return {terms[0]};")
                 lines.append("  }")
+                lines.append("#endif")
             lines.append("};")
     return "\n".join(lines) + "\n"
 
@@ -212,6 +217,43 @@ namespace yt {{
 void ader_set_attribute_o{N}_{P}_{V}(size_t smem) {{ ader_set_attribute_ve<{N}, {REAL}, {WHICH}>(smem); }}
 void ader_launch_o{N}_{P}_{V}(const AderLaunch& L) {{ ader_launch_ve<{N}, {REAL}, {WHICH}>(L); }}
 int ader_upload_o{N}_{P}_{V}(const float* vals, size_t n) {{ {UPLOAD} }}
+}}  // namespace yt
+"""
+
+BATCH_UNIT = """// Generated by codegen.py: the tile functions of the persistent batch kernel for
+// polynomial degree {N}, contraction type {REAL} (separately compiled, -rdc; values of the
+// sparse rows from global memory).
+#define YT_ROWS_GLOBAL 1
+#include "batch_kernel.cuh"
+#include "yt_rows_o{N}.cuh"
+
+namespace yt {{
+namespace {{
+__device__ __forceinline__ StepTables<{REAL}> tables_of(const BatchGroup* g) {{
+  StepTables<{REAL}> T;
+  T.val = static_cast<const {REAL}*>(g->val);
+  T.f = static_cast<const {REAL}*>(g->f);
+  T.dt = g->dt;
+  double f = 1.0;
+  for (int i = 0; i < 8; ++i) {{
+    f *= (i + 1.0);
+    T.invfact[i] = 1.0 / f;
+  }}
+  return T;
+}}
+}}  // namespace
+
+__device__ __noinline__ void batch_local_o{N}_{P}(const BatchGroup* g, const StarPattern* SP, size_t tile) {{
+  local_tile<{N}, false, {REAL}, false>(g->Q, g->Q, g->I, static_cast<{REAL}*>(g->Pface),
+                                        static_cast<{REAL}*>(g->Wloc), static_cast<const {REAL}*>(g->star),
+                                        static_cast<const {REAL}*>(g->floc), tables_of(g), *SP,
+                                        VeTables<{REAL}>{{}}, tile, g->dt);
+}}
+
+__device__ __noinline__ void batch_neigh_o{N}_{P}(const BatchGroup* g, const FaceGroups* G, size_t tile) {{
+  neigh_tile<{N}, true, {REAL}, kNq>(g->Q, *G, static_cast<const {REAL}*>(g->Wloc),
+                                     static_cast<const {REAL}*>(g->fnb), g->conn, tables_of(g), tile);
+}}
 }}  // namespace yt
 """
 
@@ -254,6 +296,9 @@ def generate(build_dir: str) -> list[str]:
             _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused, UPLOAD=upload,
                                                 REAL="double" if P == "f64" else "float"))
             units.append(unit)
+        unit = os.path.join(gen, f"ader_o{N}_{P}_batch_rdc.cu")
+        _write_if_changed(unit, BATCH_UNIT.format(N=N, P=P, REAL="double" if P == "f64" else "float"))
+        units.append(unit)
         for V, which in VE_VARIANTS.items():
             unit = os.path.join(gen, f"ader_o{N}_{P}_{V}.cu")
             if P == "f32" and N <= CONST_MAX_N:

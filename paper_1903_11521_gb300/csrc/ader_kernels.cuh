@@ -74,6 +74,16 @@ template <int N, int LIST, int ROW>
 struct Row;
 }  // namespace gen
 
+// FP32 values of degrees <= 5 come from constant memory (one copy per translation unit),
+// except in the translation units of the persistent batch kernel, which are linked into
+// one device module (YT_ROWS_GLOBAL): the constant bank could not hold every degree's
+// values at once, so they read the values from global memory.
+#ifdef YT_ROWS_GLOBAL
+constexpr bool kConstValues = false;
+#else
+constexpr bool kConstValues = true;
+#endif
+
 // Sparse row of a list.  FP64: one accumulator chain (Row::dot1; the FP64 pipe is the
 // limit and nine warps supply enough independent chains, while every extra accumulator
 // costs an add to combine).  FP32: four accumulators (Row::dot; latency is the limit),
@@ -83,7 +93,7 @@ template <int N, int LIST, int ROW, typename Real>
 __device__ __forceinline__ Real row_dot(const Real* __restrict__ v, const Real* __restrict__ x) {
   if constexpr (sizeof(Real) == 8)
     return gen::Row<N, LIST, ROW>::dot1(v, x, Real(0));
-  else if constexpr (N <= 5)
+  else if constexpr (N <= 5 && kConstValues)
     return gen::Row<N, LIST, ROW>::dotc(x);
   else
     return gen::Row<N, LIST, ROW>::dot(v, x);
@@ -99,7 +109,7 @@ __device__ __forceinline__ Real row_dot_acc(const Real* __restrict__ v, const Re
 // The same with the operand column in a register array x[0..S).
 template <int N, int LIST, int ROW, typename Real, int S>
 __device__ __forceinline__ Real row_dotr(const Real* __restrict__ v, const Real (&x)[S]) {
-  if constexpr (sizeof(Real) == 4 && N <= 5)
+  if constexpr (sizeof(Real) == 4 && N <= 5 && kConstValues)
     return gen::Row<N, LIST, ROW>::dotrc(x);
   else
     return gen::Row<N, LIST, ROW>::template dotr1<Real, S>(v, x, Real(0));
@@ -426,11 +436,13 @@ __device__ __forceinline__ void ck_ve(const StepTables<Real>& T, double dt, cons
 // VE: 27 quantities (Q, Qout, Iout are [tile][27][B][32]); the elastic rows as above
 // with the source terms, the anelastic functions' derivatives and time integral by the
 // stress warps (their volume, source and flux terms are k_theta's).
-template <int N, bool LIFT, typename Real, bool VE = false>
-__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value))
-k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
-        const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs,
-        VeTables<Real> V) {
+// local_tile: the work of one tile (tile index and time step given), shared by the
+// kernel below and the persistent batch kernel.
+template <int N, bool LIFT, typename Real, bool VE>
+__device__ __forceinline__ void local_tile(const double* Q, double* Qout, double* Iout, Real* Pface,
+                                           Real* Wloc, const Real* star, const Real* floc,
+                                           StepTables<Real> T, StarPattern SP, VeTables<Real> V,
+                                           size_t tile, double dt) {
   using Dm = Dims<N>;
   constexpr int NQT = VE ? kNqVe : kNq;      // quantities per element in Q and I
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
@@ -448,20 +460,6 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   double* Ish = RS > 0 ? reinterpret_cast<double*>(Xsh + XR * kNq * kTile) : nullptr;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  size_t tile = blockIdx.x;
-  double dt = T.dt;
-  if (refs) {
-    const TileRef& r = refs[blockIdx.x];
-    Q = r.Q;
-    Qout = r.Q;
-    Iout = r.I;
-    Pface = static_cast<Real*>(r.Pface);
-    Wloc = static_cast<Real*>(r.Wloc);
-    star = static_cast<const Real*>(r.star);
-    floc = static_cast<const Real*>(r.floc);
-    tile = (size_t)r.tile;
-    dt = r.dt;
-  }
   const double* Qt = Q + tile * (NQT * B * kTile);
   double* It = Iout + tile * (NQT * B * kTile);
 
@@ -617,6 +615,28 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
 
 }
 
+template <int N, bool LIFT, typename Real, bool VE = false>
+__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, true>::value))
+k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, const Real* star,
+        const Real* floc, StepTables<Real> T, StarPattern SP, const TileRef* __restrict__ refs,
+        VeTables<Real> V) {
+  size_t tile = blockIdx.x;
+  double dt = T.dt;
+  if (refs) {
+    const TileRef& r = refs[blockIdx.x];
+    Q = r.Q;
+    Qout = r.Q;
+    Iout = r.I;
+    Pface = static_cast<Real*>(r.Pface);
+    Wloc = static_cast<Real*>(r.Wloc);
+    star = static_cast<const Real*>(r.star);
+    floc = static_cast<const Real*>(r.floc);
+    tile = (size_t)r.tile;
+    dt = r.dt;
+  }
+  local_tile<N, LIFT, Real, VE>(Q, Qout, Iout, Pface, Wloc, star, floc, T, SP, V, tile, dt);
+}
+
 // ------------------------------------------------------------- asynchronous copies
 // Global -> shared copy of one element (4 or 8 bytes) that bypasses the registers
 // (cp.async), grouped and waited for per face.
@@ -645,10 +665,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The four faces' W (BT x 9 each) stay in shared memory; every row k of Q is then
 // updated once with sum_s Rhat^s_k. W^s (no per-row accumulator array).
 // NQT: quantities per element of Q (27 for the elastic rows of a 27-quantity step).
-template <int N, bool WITH_LOCAL, typename Real, int NQT = kNq>
-__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, false>::value))
-k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
-        StepTables<Real> T, const TileRef* __restrict__ refs) {
+template <int N, bool WITH_LOCAL, typename Real, int NQT>
+__device__ __forceinline__ void neigh_tile(double* Q, const FaceGroups& G, const Real* Wloc, const Real* fnb,
+                                           const int* conn, StepTables<Real> T, size_t tile) {
   using Dm = Dims<N>;
   using Slots = NeighSlots<N, Real>;
   constexpr int B = Dm::B, BT = Dm::BT;
@@ -658,16 +677,6 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
   Real* Wsh = reinterpret_cast<Real*>(smem_raw);  // slots x BT rows x 9 x 32
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  size_t tile = blockIdx.x;
-  if (refs) {
-    const TileRef& r = refs[blockIdx.x];
-    Q = r.Q;
-    Wloc = static_cast<const Real*>(r.Wloc);
-    fnb = static_cast<const Real*>(r.fnb);
-    conn = r.conn;
-    G.base[0] = r.Pface;        // neighbours lie in the same problem (group 0)
-    tile = (size_t)r.tile;
-  }
   const size_t e = tile * kTile + lane;
   const Real* Ft = fnb + tile * (4 * kNq * kNq * kTile);
 
@@ -759,6 +768,23 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
     lift(std::integral_constant<int, 0>{}, std::integral_constant<int, 4>{});
   else
     lift(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
+}
+
+template <int N, bool WITH_LOCAL, typename Real, int NQT = kNq>
+__global__ void __launch_bounds__(kNq * kTile, (MinBlocks<N, Real, false>::value))
+k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* conn,
+        StepTables<Real> T, const TileRef* __restrict__ refs) {
+  size_t tile = blockIdx.x;
+  if (refs) {
+    const TileRef& r = refs[blockIdx.x];
+    Q = r.Q;
+    Wloc = static_cast<const Real*>(r.Wloc);
+    fnb = static_cast<const Real*>(r.fnb);
+    conn = r.conn;
+    G.base[0] = r.Pface;        // neighbours lie in the same problem (group 0)
+    tile = (size_t)r.tile;
+  }
+  neigh_tile<N, WITH_LOCAL, Real, NQT>(Q, G, Wloc, fnb, conn, T, tile);
 }
 
 // ------------------------------------------------------------------------- K_theta

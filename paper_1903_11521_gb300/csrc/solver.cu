@@ -11,6 +11,7 @@
 
 #include "ader_kernels.cuh"
 #include "ader_tc.cuh"
+#include "batch_kernel.cuh"
 #include "common.h"
 #include "solver_internal.h"
 #include "tables.h"
@@ -287,11 +288,46 @@ struct Csr {
   int64_t row_nnz(int off, int r) const { return rp[off + r + 1] - rp[off + r]; }
 };
 
+// Allocation mode of the calling thread (solver_create_stream_ordered sets it while it
+// creates a solver): stream-ordered allocations on that stream, each followed by a
+// synchronisation of that stream so that the memory is ready for any stream.
+struct AllocMode {
+  bool async = false;
+  cudaStream_t stream = nullptr;
+};
+thread_local AllocMode t_alloc;
+
 template <typename T>
 T* dalloc(size_t n) {
   T* p = nullptr;
-  cuda_check(cudaMalloc(&p, n * sizeof(T) + 16), "cudaMalloc");
+  if (t_alloc.async) {
+    cuda_check(cudaMallocAsync(reinterpret_cast<void**>(&p), n * sizeof(T) + 16, t_alloc.stream), "cudaMallocAsync");
+    cuda_check(cudaStreamSynchronize(t_alloc.stream), "allocation sync");
+  } else {
+    cuda_check(cudaMalloc(&p, n * sizeof(T) + 16), "cudaMalloc");
+  }
   return p;
+}
+// Allocation in the mode of solver s (its buffers created after yt_solver_create).
+template <typename T>
+T* sdalloc(const yt_solver* s, size_t n) {
+  const AllocMode saved = t_alloc;
+  t_alloc.async = s->alloc_async;
+  t_alloc.stream = s->alloc_stream;
+  T* p = nullptr;
+  try {
+    p = dalloc<T>(n);
+  } catch (...) {
+    t_alloc = saved;
+    throw;
+  }
+  t_alloc = saved;
+  return p;
+}
+void dfree_temp(void* p) {
+  if (!p) return;
+  if (t_alloc.async) cudaFreeAsync(p, t_alloc.stream);
+  else cudaFree(p);
 }
 
 }  // namespace
@@ -647,6 +683,15 @@ void solver_launch_variant(yt_solver* s, const AderLaunch& L, int variant) {
   cuda_check(cudaGetLastError(), "kernel launch");
 }
 
+yt_status solver_create_stream_ordered(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
+                                       cudaStream_t stream, yt_solver** out) {
+  t_alloc.async = true;
+  t_alloc.stream = stream;
+  const yt_status rc = yt_solver_create(mesh, scheme, reinterpret_cast<yt_stream>(stream), out);
+  t_alloc = AllocMode{};
+  return rc;
+}
+
 size_t solver_device_bytes(int order, yt_precision prec, int64_t n_elements) {
   const int N = order - 1;
   const size_t B = n_basis(N), BT = n_face_basis(N);
@@ -690,6 +735,8 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
                "27-quantity solvers: YT_F64 or YT_F32");
     YT_REQUIRE(!ve || nb, YT_ERR_INVALID, "27-quantity solvers need the face connectivity");
     auto s = std::make_unique<yt_solver>();
+    s->alloc_async = t_alloc.async;
+    s->alloc_stream = t_alloc.stream;
     s->P = ve ? kNqVe : kNq;
     s->N = scheme->order - 1;
     s->B = n_basis(s->N);
@@ -791,9 +838,9 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
       }
     }
     cudaError_t e5 = cudaStreamSynchronize(st);
-    cudaFree(dmat);
-    cudaFree(djac);
-    if (datt) cudaFree(datt);
+    dfree_temp(dmat);
+    dfree_temp(djac);
+    dfree_temp(datt);
     cuda_check(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : (e4 != cudaSuccess ? e4 : e5))),
                "solver setup");
     *out = s.release();
@@ -809,7 +856,7 @@ extern "C" yt_status yt_solver_set_dofs(yt_solver* s, const double* dofs, yt_mem
     const size_t n = (size_t)s->E * s->P * s->B;
     const double* src = dofs;
     if (where == YT_MEM_HOST) {
-      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
+      if (!s->staging) s->staging = sdalloc<double>(s, (size_t)s->Epad * s->P * s->B);
       cuda_check(cudaMemcpyAsync(s->staging, dofs, n * sizeof(double), cudaMemcpyHostToDevice, st), "H2D dofs");
       src = s->staging;
     }
@@ -829,7 +876,7 @@ extern "C" yt_status yt_solver_get(yt_solver* s, yt_field field, double* out, yt
     const size_t n = (size_t)s->E * s->P * s->B;
     double* dst = out;
     if (where == YT_MEM_HOST) {
-      if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
+      if (!s->staging) s->staging = sdalloc<double>(s, (size_t)s->Epad * s->P * s->B);
       dst = s->staging;
     }
     k_from_blocked<<<blocks_for((int64_t)n, 256), 256, 0, st>>>(field == YT_FIELD_DOFS ? s->Q : s->I,
@@ -912,7 +959,7 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
     YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     constexpr int kChunks = 8;
-    if (!s->staging) s->staging = dalloc<double>((size_t)s->Epad * s->P * s->B);
+    if (!s->staging) s->staging = sdalloc<double>(s, (size_t)s->Epad * s->P * s->B);
     if (!s->copy_stream) {
       cuda_check(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "copy stream");
       cuda_check(cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming), "event");
@@ -1068,10 +1115,26 @@ struct yt_batch {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;
   cudaGraphExec_t exec = nullptr;
-  int mode = 0;                              // 0: groups in sequence, 1: groups on parallel branches
+  // 0: per-group kernels in sequence, 1: per-group kernels on parallel graph branches,
+  // 2: the persistent kernel (one cooperative launch per step)
+  int mode = 0;
+  // persistent kernel: group table, work items of both item orders ([order][phase][items]),
+  // claim / barrier counters and the status word, launch shape and chosen parameters
+  BatchGroup* d_groups = nullptr;
+  int2* d_items[2] = {nullptr, nullptr};
+  int n_items = 0;                           // tiles of all groups (per phase)
+  int* d_counters = nullptr;                 // [0..2] counters, [3] status
+  size_t pers_smem = 0;
+  unsigned pers_grid = 0;
+  bool pers_coop = true;
+  int pers_order = 0, pers_chunk = 1;
+  std::string config;                        // the chosen form and the tuner's timings
   double flops = 0.0, bytes = 0.0;
   ~yt_batch() {
     if (exec) cudaGraphExecDestroy(exec);
+    for (auto* p : d_items) if (p) cudaFree(p);
+    if (d_groups) cudaFree(d_groups);
+    if (d_counters) cudaFree(d_counters);
     for (auto* g : groups) delete g;
     for (auto* p : d_offs) cudaFree(p);
     for (auto* p : d_conn) cudaFree(p);
@@ -1093,6 +1156,21 @@ AderLaunch batch_launch_args(yt_batch* b, size_t g, cudaStream_t st) {
 
 void batch_record(yt_batch* b, cudaStream_t st, int mode) {
   const size_t G = b->groups.size();
+  if (mode == 2) {
+    cuda_check(cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(int), st), "reset counters");
+    BatchArgs A{};
+    A.groups = b->d_groups;
+    A.faces = b->faces;
+    A.items = b->d_items[b->pers_order];
+    A.n_items[0] = A.n_items[1] = b->n_items;
+    A.chunk = b->pers_chunk;
+    A.counters = b->d_counters;
+    A.status = b->d_counters + 3;
+    A.SP = kStar;
+    cuda_check(batch_persistent_launch(b->prec != YT_F64, A, b->pers_grid, b->pers_smem, st, b->pers_coop),
+               "persistent batch launch");
+    return;
+  }
   // (YT_VARIANT_SWITCH dispatches on the degree and precision of the solver named `s`)
   auto local = [&](size_t g, cudaStream_t stream) {
     const AderLaunch L = batch_launch_args(b, g, stream);
@@ -1122,7 +1200,7 @@ void batch_record(yt_batch* b, cudaStream_t st, int mode) {
   }
 }
 
-cudaGraphExec_t batch_graph(yt_batch* b, int mode) {
+cudaGraphExec_t batch_graph_once(yt_batch* b, int mode) {
   cudaGraph_t graph = nullptr;
   cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
   try {
@@ -1130,6 +1208,7 @@ cudaGraphExec_t batch_graph(yt_batch* b, int mode) {
   } catch (...) {
     cudaStreamEndCapture(b->capture, &graph);
     if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
     throw;
   }
   cuda_check(cudaStreamEndCapture(b->capture, &graph), "end capture");
@@ -1138,6 +1217,95 @@ cudaGraphExec_t batch_graph(yt_batch* b, int mode) {
   cudaGraphDestroy(graph);
   cuda_check(e, "graph instantiate");
   return exec;
+}
+
+// The persistent kernel is recorded as a cooperative launch (every CTA resident, which
+// its grid barrier needs); should capture refuse that, it is recorded as a plain launch
+// of the same grid, which the occupancy query sized to fit the device at once.
+cudaGraphExec_t batch_graph(yt_batch* b, int mode) {
+  if (mode != 2 || !b->pers_coop) return batch_graph_once(b, mode);
+  try {
+    return batch_graph_once(b, mode);
+  } catch (const Error&) {
+    b->pers_coop = false;
+    return batch_graph_once(b, mode);
+  }
+}
+
+// Work items (group, tile) of the persistent kernel in two orders: 0 = groups by
+// decreasing degree (the longest tiles first), 1 = groups interleaved tile by tile.
+void batch_items(yt_batch* b) {
+  const size_t G = b->groups.size();
+  std::vector<int> by_degree(G);
+  for (size_t g = 0; g < G; ++g) by_degree[g] = (int)g;
+  std::sort(by_degree.begin(), by_degree.end(), [&](int a, int c) { return b->group_n[a] > b->group_n[c]; });
+  std::vector<int2> order0, order1;
+  for (int g : by_degree)
+    for (int64_t t = 0; t < b->groups[g]->ntiles; ++t) order0.push_back(make_int2(g, (int)t));
+  int64_t maxt = 0;
+  for (auto* s : b->groups) maxt = std::max<int64_t>(maxt, s->ntiles);
+  for (int64_t t = 0; t < maxt; ++t)
+    for (int g : by_degree)
+      if (t < b->groups[g]->ntiles) order1.push_back(make_int2(g, (int)t));
+  b->n_items = (int)order0.size();
+  int o = 0;
+  for (auto* v : {&order0, &order1}) {
+    std::vector<int2> both(*v);
+    both.insert(both.end(), v->begin(), v->end());      // local phase, then neighbour phase
+    b->d_items[o] = dalloc<int2>(both.size());
+    cuda_check(cudaMemcpy(b->d_items[o], both.data(), both.size() * sizeof(int2), cudaMemcpyHostToDevice), "copy items");
+    ++o;
+  }
+}
+
+// Group table, shared memory and grid of the persistent kernel.
+void batch_persistent_setup(yt_batch* b) {
+  const size_t G = b->groups.size();
+  std::vector<BatchGroup> tab(G);
+  size_t smem = 0;
+  for (size_t g = 0; g < G; ++g) {
+    yt_solver* s = b->groups[g];
+    BatchGroup& t = tab[g];
+    t.N = s->N;
+    t.Q = s->Q;
+    t.I = s->I;
+    t.Pface = s->Pface;
+    t.Wloc = s->Wloc;
+    t.star = s->star_r;
+    t.floc = s->floc_r;
+    t.fnb = s->fnb_r;
+    t.conn = b->d_conn[g];
+    const bool f32 = s->prec != YT_F64;
+    t.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
+    t.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
+    t.dt = s->dt;
+    smem = std::max(smem, std::max(s->smem_local, s->smem_neigh));
+  }
+  b->d_groups = dalloc<BatchGroup>(G);
+  cuda_check(cudaMemcpy(b->d_groups, tab.data(), G * sizeof(BatchGroup), cudaMemcpyHostToDevice), "copy groups");
+  b->d_counters = dalloc<int>(4);
+  cuda_check(cudaMemset(b->d_counters, 0, 4 * sizeof(int)), "memset counters");
+  batch_items(b);
+  b->pers_smem = smem;
+  const int per_sm = batch_persistent_prepare(b->prec != YT_F64, smem);
+  cudaGetLastError();
+  if (per_sm <= 0) {               // the persistent form is then unavailable (set_form refuses it)
+    b->pers_grid = 0;
+    return;
+  }
+  int dev = 0, sms = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  b->pers_grid = (unsigned)std::min<int64_t>((int64_t)per_sm * sms, b->n_items);
+}
+
+std::string batch_describe(const yt_batch* b) {
+  if (b->mode == 0) return "per-group kernels in sequence (one graph launch per step)";
+  if (b->mode == 1) return "per-group kernels on parallel graph branches (one graph launch per step)";
+  return "persistent kernel: " + std::string(b->pers_coop ? "cooperative" : "occupancy-sized") +
+         " launch of " + std::to_string(b->pers_grid) + " CTAs x 288 threads, " +
+         std::to_string(b->pers_smem) + " B shared memory, " + std::to_string(b->pers_chunk) +
+         " tile(s) per claim, items " + (b->pers_order == 0 ? "by decreasing degree" : "interleaved across degrees");
 }
 
 }  // namespace
@@ -1230,7 +1398,9 @@ extern "C" yt_status yt_batch_create(const yt_mesh_desc* mesh, const int8_t* ord
     b->ev.resize(b->groups.size() + 1);
     for (auto& e : b->ev) cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
     cuda_check(cudaStreamSynchronize(st), "batch setup");
+    batch_persistent_setup(b.get());
     b->exec = batch_graph(b.get(), b->mode);
+    b->config = batch_describe(b.get());
     *out = b.release();
   });
 }
@@ -1286,8 +1456,11 @@ extern "C" yt_status yt_batch_tune(yt_batch* b, int32_t repeats, yt_stream strea
     YT_REQUIRE(b, YT_ERR_INVALID, "null batch");
     YT_REQUIRE(repeats > 0 && repeats <= 1000, YT_ERR_INVALID, "repeats must be 1..1000");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // time each candidate graph on the caller's data and keep the fastest; the DOFs are
-    // saved before and restored after, so tuning leaves the state unchanged
+    // time each candidate on the caller's data and keep the fastest; the DOFs are saved
+    // before and restored after, so tuning leaves the state unchanged.  Candidates: the
+    // per-group kernels in sequence and on parallel branches, and the persistent kernel
+    // with each item order (by decreasing degree / interleaved) and 1, 2 or 4 tiles per
+    // claim.
     const size_t G = b->groups.size();
     std::vector<double*> backup(G, nullptr);
     for (size_t g = 0; g < G; ++g) {
@@ -1299,10 +1472,18 @@ extern "C" yt_status yt_batch_tune(yt_batch* b, int32_t repeats, yt_stream strea
     cudaEvent_t t0, t1;
     cuda_check(cudaEventCreate(&t0), "event");
     cuda_check(cudaEventCreate(&t1), "event");
+    struct Cand { int mode, order, chunk; };
+    std::vector<Cand> cands = {{0, 0, 1}, {1, 0, 1}};
+    if (b->pers_grid > 0)
+      for (int order = 0; order < 2; ++order)
+        for (int chunk : {1, 2, 4}) cands.push_back({2, order, chunk});
     float best = 0.0f;
-    int best_mode = b->mode;
-    for (int mode = 0; mode < 2; ++mode) {
-      cudaGraphExec_t ex = batch_graph(b, mode);
+    size_t best_i = 0;
+    std::string table;
+    for (size_t i = 0; i < cands.size(); ++i) {
+      b->pers_order = cands[i].order;
+      b->pers_chunk = cands[i].chunk;
+      cudaGraphExec_t ex = batch_graph(b, cands[i].mode);
       cuda_check(cudaGraphLaunch(ex, st), "warm-up");
       cuda_check(cudaEventRecord(t0, st), "event");
       for (int r = 0; r < repeats; ++r) cuda_check(cudaGraphLaunch(ex, st), "graph launch");
@@ -1310,9 +1491,15 @@ extern "C" yt_status yt_batch_tune(yt_batch* b, int32_t repeats, yt_stream strea
       cuda_check(cudaEventSynchronize(t1), "sync");
       float ms = 0.0f;
       cuda_check(cudaEventElapsedTime(&ms, t0, t1), "elapsed");
-      if (mode == 0 || ms < best) {
+      ms /= (float)repeats;
+      table += (i ? "; " : "") + std::string(cands[i].mode == 0 ? "sequence" : (cands[i].mode == 1 ? "branches" : "persistent")) +
+               (cands[i].mode == 2 ? std::string(cands[i].order == 0 ? " by-degree" : " interleaved") + " chunk " +
+                                         std::to_string(cands[i].chunk)
+                                   : std::string()) +
+               " " + std::to_string(ms) + " ms";
+      if (i == 0 || ms < best) {
         best = ms;
-        best_mode = mode;
+        best_i = i;
       }
       cudaGraphExecDestroy(ex);
     }
@@ -1323,15 +1510,54 @@ extern "C" yt_status yt_batch_tune(yt_batch* b, int32_t repeats, yt_stream strea
       const size_t n = (size_t)s->Epad * kNq * s->B;
       cuda_check(cudaMemcpyAsync(s->Q, backup[g], n * sizeof(double), cudaMemcpyDeviceToDevice, st), "restore");
     }
+    cuda_check(cudaMemsetAsync(b->d_counters + 3, 0, sizeof(int), st), "status reset");
     cuda_check(cudaStreamSynchronize(st), "restore sync");
     for (auto* p : backup) cudaFree(p);
-    if (best_mode != b->mode) {
-      cudaGraphExec_t ex = batch_graph(b, best_mode);
-      cudaGraphExecDestroy(b->exec);
-      b->exec = ex;
-      b->mode = best_mode;
-    }
+    b->pers_order = cands[best_i].order;
+    b->pers_chunk = cands[best_i].chunk;
+    cudaGraphExec_t ex = batch_graph(b, cands[best_i].mode);
+    cudaGraphExecDestroy(b->exec);
+    b->exec = ex;
+    b->mode = cands[best_i].mode;
+    b->config = batch_describe(b) + " (tuned: " + table + ")";
     if (chosen) *chosen = b->mode;
+  });
+}
+
+extern "C" yt_status yt_batch_config(const yt_batch* b, char* out, int32_t capacity) {
+  return guarded([&] {
+    YT_REQUIRE(b && out && capacity > 0, YT_ERR_INVALID, "null argument");
+    std::strncpy(out, b->config.c_str(), (size_t)capacity - 1);
+    out[capacity - 1] = '\0';
+  });
+}
+
+extern "C" yt_status yt_batch_set_form(yt_batch* b, int32_t form, int32_t order, int32_t chunk) {
+  return guarded([&] {
+    YT_REQUIRE(b, YT_ERR_INVALID, "null batch");
+    YT_REQUIRE(form >= 0 && form <= 2 && order >= 0 && order <= 1 && (chunk == 1 || chunk == 2 || chunk == 4),
+               YT_ERR_INVALID, "form 0..2, order 0..1, chunk 1, 2 or 4");
+    YT_REQUIRE(form != 2 || b->pers_grid > 0, YT_ERR_UNSUPPORTED, "the persistent kernel does not fit an SM");
+    b->pers_order = order;
+    b->pers_chunk = chunk;
+    cudaGraphExec_t ex = batch_graph(b, form);
+    cudaGraphExecDestroy(b->exec);
+    b->exec = ex;
+    b->mode = form;
+    b->config = batch_describe(b);
+  });
+}
+
+extern "C" yt_status yt_batch_status(yt_batch* b, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(b, YT_ERR_INVALID, "null batch");
+    cuda_check(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "stream synchronize");
+    int v = 0;
+    cuda_check(cudaMemcpy(&v, b->d_counters + 3, sizeof(int), cudaMemcpyDeviceToHost), "status copy");
+    if (v != 0) {
+      cuda_check(cudaMemset(b->d_counters + 3, 0, sizeof(int)), "status reset");
+      throw Error(YT_ERR_TIMEOUT, "the grid barrier of the persistent batch kernel ran out");
+    }
   });
 }
 

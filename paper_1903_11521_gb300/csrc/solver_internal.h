@@ -42,15 +42,24 @@ struct yt_solver {
   double *cth = nullptr, *om = nullptr, *fthl = nullptr, *fthn = nullptr;
   void *cth_r = nullptr, *om_r = nullptr, *fthl_r = nullptr, *fthn_r = nullptr, *theta = nullptr;
   size_t smem_theta = 0;
+  // device memory from the stream-ordered allocator on alloc_stream (solvers of a server),
+  // else from cudaMalloc
+  bool alloc_async = false;
+  cudaStream_t alloc_stream = nullptr;
   // yt_step_host: copy stream and per-chunk events (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   cudaEvent_t ev_in[16] = {}, ev_out[16] = {};
+  void free_device(void* p) {
+    if (!p) return;
+    if (alloc_async) cudaFreeAsync(p, alloc_stream);
+    else cudaFree(p);
+  }
   ~yt_solver() {
     if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
     if (cth_r == (void*)cth) cth_r = om_r = fthl_r = fthn_r = nullptr;
     for (void* p : {(void*)cth, (void*)om, (void*)fthl, (void*)fthn, cth_r, om_r, fthl_r, fthn_r, theta})
-      if (p) cudaFree(p);
+      free_device(p);
     for (cudaEvent_t e : ev_in) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_out) if (e) cudaEventDestroy(e);
     if (ev_start) cudaEventDestroy(ev_start);
@@ -60,7 +69,7 @@ struct yt_solver {
                     floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
                     (void*)d_val32, (void*)d_f32, (void*)d_tc_local, (void*)d_tc_neigh, (void*)d_tc_scratch,
                     (void*)d_status})
-      if (p) cudaFree(p);
+      free_device(p);
   }
 };
 
@@ -73,4 +82,9 @@ AderLaunch solver_launch_args(yt_solver* s, cudaStream_t st);
 void solver_launch_variant(yt_solver* s, const AderLaunch& L, int variant);
 // Device bytes a solver of this order / precision / size allocates (its tables aside).
 size_t solver_device_bytes(int order, yt_precision prec, int64_t n_elements);
+// yt_solver_create with every device allocation of the solver taken from the
+// stream-ordered allocator on `stream` (and freed there by yt_solver_destroy): creating
+// and destroying solvers then never waits for work on other streams.
+yt_status solver_create_stream_ordered(const yt_mesh_desc* mesh, const yt_scheme_desc* scheme,
+                                       cudaStream_t stream, yt_solver** out);
 }  // namespace yt

@@ -221,6 +221,21 @@ class Batch:
                    "yt_batch_tune")
         return chosen.value
 
+    def set_form(self, form: int, order: int = 0, chunk: int = 1):
+        """0: per-degree kernels in sequence, 1: on parallel branches, 2: the persistent
+        kernel (order 0 by decreasing degree / 1 interleaved, chunk tiles per claim)."""
+        _lib.check(self.lib.yt_batch_set_form(self.handle, form, order, chunk), "yt_batch_set_form")
+
+    def config(self) -> str:
+        buf = C.create_string_buffer(4096)
+        _lib.check(self.lib.yt_batch_config(self.handle, buf, 4096), "yt_batch_config")
+        return buf.value.decode()
+
+    def status(self, stream=None):
+        """Synchronises; raises YtError (YT_ERR_TIMEOUT) if the persistent kernel's grid
+        barrier ran out."""
+        _lib.check(self.lib.yt_batch_status(self.handle, _stream_handle(stream)), "yt_batch_status")
+
     def stats(self):
         f, b, g = C.c_double(), C.c_double(), C.c_int32()
         _lib.check(self.lib.yt_batch_stats(self.handle, C.byref(f), C.byref(b), C.byref(g)), "yt_batch_stats")
