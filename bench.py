@@ -85,6 +85,9 @@ def parse():
                          "(for profiling one form)")
     ap.add_argument("--form-steps", type=int, default=10,
                     help="steps of the 27-quantity form at full size (--form viscoelastic)")
+    ap.add_argument("--form-n", type=int, default=55,
+                    help="cubes per direction of the 27-quantity form's mesh (--form viscoelastic; "
+                         "55: 998,250 tets; smaller for profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batching and serving measurements")
     return ap.parse_args()
@@ -306,6 +309,31 @@ def form_precision(yt, order, E, steps, stream, precision="f32"):
     return out
 
 
+def mass_diagonal(yt, order):
+    """Diagonal of the library's reference mass matrix (the basis is orthogonal; the
+    library returns M as its B diagonal entries)."""
+    B = order * (order + 1) * (order + 2) // 6
+    m = yt.reference_matrix(order, "M")
+    return m if m.size == B else np.diag(m.reshape(B, B))
+
+
+def elastic_energy(q, el, Mk, chunk=65536):
+    """Elastic energy 1/2 int (rho |v|^2 + sigma : S sigma) of DOFs q (E, B, >= 9): the mass
+    matrix of the basis is diagonal, so per element it is
+    1/2 |J| sum_k M_kk (rho |v_k|^2 + sigma_k : S sigma_k), S the isotropic compliance:
+    sigma : S sigma = (sigma : sigma - lambda / (3 lambda + 2 mu) tr(sigma)^2) / (2 mu)."""
+    det = np.abs(np.linalg.det(el.jac))
+    tot = 0.0
+    for i in range(0, q.shape[0], chunk):
+        d = q[i:i + chunk]
+        rho, lam, mu = el.rho[i:i + chunk, None], el.lam[i:i + chunk, None], el.mu[i:i + chunk, None]
+        ss = (d[..., 0:3] ** 2).sum(-1) + 2.0 * (d[..., 3:6] ** 2).sum(-1)
+        tr = d[..., 0:3].sum(-1)
+        dens = rho * (d[..., 6:9] ** 2).sum(-1) + (ss - lam / (3 * lam + 2 * mu) * tr ** 2) / (2 * mu)
+        tot += 0.5 * float((det[i:i + chunk, None] * Mk[None, :] * dens).sum())
+    return tot
+
+
 def form_structured(yt, stream, n=55, steps=100):
     """100 steps on a jittered periodic structured mesh of n^3 cubes x 6 tets (n = 55:
     998,250 tets; vertices moved by up to 0.1 h, homogeneous material at the middle of the
@@ -342,24 +370,8 @@ def form_structured(yt, stream, n=55, steps=100):
             acc += np.einsum('ebq,ebq->q', d, d)
         return acc
 
-    det = np.abs(np.linalg.det(el.jac))
-
-    def energy(q, order, chunk=65536):
-        # elastic energy 1/2 int (rho |v|^2 + sigma : S sigma) of the discrete solution:
-        # the mass matrix of the basis is diagonal, so per element
-        # 1/2 |J| sum_k M_kk (rho |v_k|^2 + sigma_k : S sigma_k), S the isotropic compliance
-        # sigma : S sigma = (sigma : sigma - lambda / (3 lambda + 2 mu) tr(sigma)^2) / (2 mu)
-        B = order * (order + 1) * (order + 2) // 6
-        Mk = np.diag(yt.reference_matrix(order, "M").reshape(B, B))
-        tot = 0.0
-        for i in range(0, E, chunk):
-            d = q[i:i + chunk]
-            rho, lam, mu = el.rho[i:i + chunk, None], el.lam[i:i + chunk, None], el.mu[i:i + chunk, None]
-            ss = (d[..., 0:3] ** 2).sum(-1) + 2.0 * (d[..., 3:6] ** 2).sum(-1)
-            tr = d[..., 0:3].sum(-1)
-            dens = rho * (d[..., 6:9] ** 2).sum(-1) + (ss - lam / (3 * lam + 2 * mu) * tr ** 2) / (2 * mu)
-            tot += 0.5 * float((det[i:i + chunk, None] * Mk[None, :] * dens).sum())
-        return tot
+    def energy(q, order):
+        return elastic_energy(q, el, mass_diagonal(yt, order))
 
     def compare(order, forms):
         B = order * (order + 1) * (order + 2) // 6
@@ -574,15 +586,29 @@ def form_batching(yt, E, precision, lo, hi, steps, stream):
     flat = rng.standard_normal(int(b.offsets[-1]))
     b._host_in = flat
     b.set_dofs_ptr(flat.ctypes.data, yt.YT_MEM_HOST, stream=stream)
+    # every form timed on the same data (each from the same starting DOFs), then the
+    # tuner's choice
+    forms = {}
+    for name, form, order, chunk in (("per_degree_kernels_sequence", 0, 0, 1),
+                                     ("per_degree_kernels_branches", 1, 0, 1),
+                                     ("persistent_by_degree_chunk1", 2, 0, 1)):
+        b.set_form(form, order, chunk)
+        b.set_dofs_ptr(flat.ctypes.data, yt.YT_MEM_HOST, stream=stream)
+        forms[name] = _timed(lambda: b.step(stream=stream), steps, 2, stream)
+    b.status(stream=stream)
+    b.set_dofs_ptr(flat.ctypes.data, yt.YT_MEM_HOST, stream=stream)
     chosen = b.tune(3, stream=stream)
     ms = _timed(lambda: b.step(stream=stream), steps, 2, stream)
+    b.status(stream=stream)
     st = b.stats()
+    cfg = b.config()
     b.close()
     return {"workload": f"p-adaptive mesh, {E} tets, per-element order U{{{lo}..{hi}}}, "
                         f"{'FP32' if precision == yt.YT_F32 else 'FP64'}",
             "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms,
-            "graph": "one CUDA graph launch per step; tuner chose "
-                     + ("parallel branches" if chosen == 1 else "groups in sequence"),
+            "chosen_form": ["per-degree kernels in sequence", "per-degree kernels on parallel branches",
+                            "persistent kernel"][chosen],
+            "tuner": cfg, "ms_per_step_by_form": forms,
             "groups": st["groups"], "achieved_tflops": st["flops"] / (ms / 1e3) / 1e12}
 
 
@@ -590,15 +616,24 @@ def form_serving(yt, n_requests=256, rate=20.0, steps=100, budget=64 << 30):
     import threading as th
     rng = np.random.default_rng(wl.SEED + 700)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_requests)).astype(int)
+    target = np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_requests))
     orders = rng.integers(3, 7, n_requests)
+    # every solve runs 100 steps, so its mesh must be a real mesh: the jittered periodic
+    # structured mesh of n^3 x 6 tets with n^3 x 6 nearest to the drawn size (one mesh per
+    # n, 1,296 .. 196,608 tets), homogeneous material, impedance-scaled N(0,1) DOFs
+    ns = np.clip(np.rint((target / 6.0) ** (1.0 / 3.0)).astype(int), 6, 32)
+    sizes = 6 * ns ** 3
+    meshes = {}
+    for n in sorted(set(int(x) for x in ns)):
+        meshes[n] = wl.jittered_periodic_mesh(n, jitter=0.1, seed=wl.SEED + 750 + n, length=100.0 * n,
+                                             rho=2500.0, lam=2.5e10, mu=2.5e10)
     reqs = []
     for i in range(n_requests):
-        E, o = int(sizes[i]), int(orders[i])
-        el = wl.random_elements(E, seed=wl.SEED + 10000 + 3 * i)
-        conn = wl.random_connectivity(E, seed=wl.SEED + 10001 + 3 * i)
-        Q = np.random.default_rng(wl.SEED + 10002 + 3 * i).standard_normal(
-            (E, o * (o + 1) * (o + 2) // 6, 9))
+        n, o = int(ns[i]), int(orders[i])
+        el, conn = meshes[n].elements, meshes[n].conn
+        E = el.rho.size
+        Q = wl.random_dofs(E, o * (o + 1) * (o + 2) // 6, seed=wl.SEED + 10002 + 3 * i, scale="impedance",
+                           elements=el)
         reqs.append((o, wl.cfl_time_step(el, o - 1), np.stack([el.rho, el.lam, el.mu], 1), el.jac,
                      conn.neighbours, conn.faces, conn.orient, Q))
     srv = yt.Server(budget, precision=yt.YT_F32)
@@ -615,18 +650,22 @@ def form_serving(yt, n_requests=256, rate=20.0, steps=100, budget=64 << 30):
     thread = th.Thread(target=submitter)
     thread.start()
     thread.join()
-    lat, queue = [], []
-    for rid in ids:
-        _, l, q = srv.wait(rid)
+    subset = set(range(0, n_requests, 8))          # results kept for the FP64 comparison
+    lat, queue, served = [], [], {}
+    for i, rid in enumerate(ids):
+        q_out, l, q = srv.wait(rid)
         lat.append(l)
         queue.append(q)
+        if i in subset:
+            served[i] = q_out
     t_end = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     lat = np.array(lat) * 1e3
     out = {"workload": f"{n_requests} independent elastic solves, Poisson arrivals {rate}/s, "
-                       f"sizes log-U[1e3, 2e5] tets, orders U{{3..6}}, {steps} steps each, FP32 "
-                       f"contractions / FP64 accumulation, HBM budget {budget >> 30} GiB",
+                       f"sizes log-U[1e3, 2e5] tets (jittered periodic meshes of n^3 x 6 tets, n = 6..32), "
+                       f"orders U{{3..6}}, {steps} steps each, FP32 contractions / FP64 accumulation, "
+                       f"HBM budget {budget >> 30} GiB",
            "solves_per_s": n_requests / t_end, "p50_latency_ms": float(np.percentile(lat, 50)),
            "p99_latency_ms": float(np.percentile(lat, 99)),
            "p50_queue_ms": float(np.percentile(np.array(queue) * 1e3, 50)),
@@ -658,6 +697,48 @@ def form_serving(yt, n_requests=256, rate=20.0, steps=100, budget=64 << 30):
         "p99_latency_ms": float(np.percentile(plain_lat, 99)),
         "element_updates_per_s": st["element_updates"] / finish, "makespan_s": finish,
         "busy_s": float(np.sum(service))}
+    # the plain FP64 path: every 8th request measured alone in FP64 (its final DOFs kept);
+    # the error of the served FP32 result of the same request against it; the FP64
+    # service time of every request from a per-order fit t = a + b E of the measured ones,
+    # and first-in-first-out queueing on the same arrivals from those times
+    svc64, errs = {}, []
+    for i in sorted(subset):
+        r = reqs[i]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s = yt.Solver(*r[:7], precision=yt.YT_F64)
+        s.set_dofs_host(r[7])
+        for _ in range(steps):
+            s.step()
+        q64 = s.get_host()
+        s.close()
+        svc64[i] = time.perf_counter() - t
+        num = np.sqrt(((served[i] - q64) ** 2).sum((0, 1)))
+        errs.append(float((num / np.sqrt((q64 ** 2).sum((0, 1)))).max()))
+        del q64
+    fit = {}
+    for o in sorted(set(int(x) for x in orders)):
+        idx = [i for i in svc64 if int(orders[i]) == o]
+        A = np.stack([np.ones(len(idx)), sizes[idx].astype(float)], 1)
+        fit[o] = np.linalg.lstsq(A, np.array([svc64[i] for i in idx]), rcond=None)[0]
+    pred = [svc64.get(i, float(fit[int(orders[i])][0] + fit[int(orders[i])][1] * sizes[i]))
+            for i in range(n_requests)]
+    finish64, lat64 = 0.0, []
+    for a, sv in zip(arrivals, pred):
+        finish64 = max(finish64, a) + sv
+        lat64.append(finish64 - a)
+    lat64 = np.array(lat64) * 1e3
+    out["plain_fp64_one_at_a_time"] = {
+        "solves_per_s": n_requests / finish64, "p50_latency_ms": float(np.percentile(lat64, 50)),
+        "p99_latency_ms": float(np.percentile(lat64, 99)), "makespan_s": finish64,
+        "busy_s": float(np.sum(pred)), "measured_solves": len(svc64),
+        "method": f"{len(svc64)} of the {n_requests} requests (every 8th) run alone in FP64 and timed; "
+                  "the others' service times from a per-order fit t = a + b E of those; FIFO queueing "
+                  "on the same arrivals"}
+    out["served_fp32_error_vs_fp64"] = {
+        "max": max(errs), "median": float(np.median(errs)), "requests": len(errs),
+        "definition": f"after {steps} steps: max over quantities of ||Q_served - Q_fp64||_F / ||Q_fp64||_F, "
+                      "the same request run alone in FP64"}
     return out
 
 
@@ -682,7 +763,8 @@ def run_ours(args):
         stream = torch.cuda.current_stream()
         run = {"executor": lambda: form_executor(yt, stream),
                "structured": lambda: form_structured(yt, stream),
-               "viscoelastic": lambda: form_viscoelastic(yt, stream, steps=args.form_steps),
+               "viscoelastic": lambda: form_viscoelastic(yt, stream, n=args.form_n, steps=args.form_steps,
+                                                         steps_long=0 if args.form_n != 55 else 100),
                "serving": lambda: form_serving(yt),
                "local_update": lambda: form_local_update(yt, 4, 1000, 200, stream)}[args.form]
         print(json.dumps({"form": args.form, "result": run()}), flush=True)
@@ -691,16 +773,31 @@ def run_ours(args):
     N = args.order - 1
     B = args.order * (args.order + 1) * (args.order + 2) // 6
     E = args.elements
-    seed = wl.SEED + 1000 * rank
-    el = wl.random_elements(E, seed=seed)
-    conn = wl.random_connectivity(E, seed=seed + 2)
-    Q = wl.random_dofs(E, B, seed=seed + 1)
-    dt = wl.cfl_time_step(el, N)
     stream = torch.cuda.current_stream()
     prec = precision_code(yt, args.precision)
-    solver = yt.Solver(args.order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac,
-                       conn.neighbours, conn.faces, conn.orient, precision=prec, stream=stream)
-    solver.set_dofs_host(Q, stream=stream)
+    part = None
+    if ws > 1:
+        # one mesh of ws x E elements (the same recipe) partitioned in blocks: E per rank,
+        # one halo exchange of face projections per step over NCCL
+        from paper_1903_11521_gb300 import partition
+        el = wl.random_elements(ws * E, seed=wl.SEED)
+        conn = wl.random_connectivity(ws * E, seed=wl.SEED + 2)
+        dt = wl.cfl_time_step(el, N)
+        import torch.distributed as dist
+        part = partition.PartitionedSolver(args.order, dt, el, conn, partition.block_partition(ws * E, ws),
+                                           rank, dist, precision=prec, stream=stream, staging="device")
+        Q = wl.random_dofs(part.ids.size, B, seed=wl.SEED + 1 + 1000 * rank)
+        part.set_dofs_local(Q)
+        solver = part.solver
+        E = part.ids.size
+    else:
+        el = wl.random_elements(E, seed=wl.SEED)
+        conn = wl.random_connectivity(E, seed=wl.SEED + 2)
+        Q = wl.random_dofs(E, B, seed=wl.SEED + 1)
+        dt = wl.cfl_time_step(el, N)
+        solver = yt.Solver(args.order, dt, np.stack([el.rho, el.lam, el.mu], 1), el.jac,
+                           conn.neighbours, conn.faces, conn.orient, precision=prec, stream=stream)
+        solver.set_dofs_host(Q, stream=stream)
     torch.cuda.synchronize()
     stats = solver.stats()
 
@@ -710,8 +807,28 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def full_step():
+        if part is not None:
+            part.step()
+        else:
+            solver.step(stream=stream)
+
+    def rest_of_step():
+        # phase 1: with a partition, the halo gather, the neighbour kernel of the interior
+        # tiles, the exchange and the neighbour kernel of the boundary tiles
+        if part is None:
+            solver.step_phase(1, stream=stream)
+            return
+        if sum(part.send_counts):
+            solver.halo_pack(part.send_buf.data_ptr(), stream=stream)
+        solver.step_phase_tiles(1, 0, part.n_interior_tiles, stream=stream)
+        part._exchange()
+        if part.n_halo:
+            solver.halo_unpack(part.recv_buf.data_ptr(), stream=stream)
+        solver.step_phase_tiles(1, part.n_interior_tiles, part.n_tiles - part.n_interior_tiles, stream=stream)
+
     for _ in range(args.warmup):
-        solver.step(stream=stream)
+        full_step()
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     clocks = ClockSampler(local)
@@ -722,7 +839,7 @@ def run_ours(args):
         ev[k][0].record(stream)
         solver.step_phase(0, stream=stream)
         ev[k][1].record(stream)
-        solver.step_phase(1, stream=stream)
+        rest_of_step()
         ev[k][2].record(stream)
     barrier()
     clk = clocks.stop()
@@ -740,7 +857,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), H2D + step + D2H per step
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and part is None:
         canon = torch.empty((E, 9, B), dtype=torch.float64, pin_memory=True)
         canon.numpy()[:] = Q.transpose(0, 2, 1)
         out = torch.empty_like(canon, pin_memory=True)
@@ -782,6 +899,34 @@ def run_ours(args):
                "overlap_fraction": max(0.0, min(1.0, (seq_ms - e_ms / K) / (h2d_ms + d2h_ms))),
                "overlap_definition": "(H2D + device step + D2H, each alone) - e2e step, over the "
                                      "copy time: the share of the copies hidden under the kernels"}
+    if not args.no_e2e and part is not None:
+        # partitioned: every step uploads this rank's DOFs from pinned host memory, runs
+        # the partitioned step (with its exchange) and downloads the result
+        canon = torch.empty((E, 9, B), dtype=torch.float64, pin_memory=True)
+        canon.numpy()[:] = Q.transpose(0, 2, 1)
+        out = torch.empty_like(canon, pin_memory=True)
+
+        def host_step():
+            solver.set_dofs_ptr(canon.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+            part.step()
+            solver.get_ptr(yt.YT_FIELD_DOFS, out.data_ptr(), yt.YT_MEM_HOST, stream=stream)
+        host_step()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            host_step()
+        b.record(stream)
+        barrier()
+        e_ms = a.elapsed_time(b)
+        import torch.distributed as dist
+        tt = torch.tensor([e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+        nbytes = E * 9 * B * 8
+        e2e = {"value": ws * E * K / (e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms / K,
+               "definition": "per rank: H2D of its DOFs, the partitioned step, D2H of its DOFs"}
     solver.close()
 
     if rank != 0:
@@ -832,7 +977,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
+            "config": workload_config(args, {"parallelism": (f"element partition over {ws} GPUs ({E} tets each, "
+                                                             "one NCCL halo exchange of face projections per step)")
+                                             if ws > 1 else "one GPU"}),
             "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
             "gpu_launches": 2 * K,
             "kernel_ms": {"k_local": local_ms, "k_neigh": neigh_ms},
@@ -869,7 +1016,9 @@ def run_reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, {"parallelism": f"independent problem per GPU x{ws}"}),
+            "config": workload_config(args, {"parallelism": (f"element partition over {ws} GPUs ({args.elements} "
+                                                             "tets each, one NCCL halo exchange of face projections "
+                                                             "per step)") if ws > 1 else "one GPU"}),
             "sample_elements": n,
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": workers, "kind": "oracle",
                              "sample": sample},

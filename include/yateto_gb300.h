@@ -180,6 +180,10 @@ typedef struct yt_mesh_desc {
   const int8_t* orient;      /* host, E x 4: orientation h (0..2) */
   const double* attenuation; /* host, E x 3 x 3: (omega_l, Y^lambda_l, Y^mu_l) of the
                                 mechanisms l = 0..2, for 27-quantity solvers; else NULL */
+  int64_t n_halo;            /* partitioned solves: number of halo slots (else 0); a
+                                neighbour entry -1 - t (t < n_halo) means that face's
+                                neighbour lives on another rank and its face projection
+                                is slot t of the halo block (yt_solver_halo_buffer) */
 } yt_mesh_desc;
 
 typedef struct yt_scheme_desc {
@@ -252,6 +256,32 @@ yt_status yt_step_phase(struct yt_solver* solver, int32_t phase, yt_stream strea
  * the device (yt_solver_get). */
 yt_status yt_step_host(struct yt_solver* solver, const double* dofs_in, double* dofs_out,
                        yt_stream stream);
+/* ---------------------------------------------------------------- partitioned solves
+ * The step shards by elements with one exchange per step: after phase 0 every rank holds
+ * the face projections R^jT I of its own elements; phase 1 of an element whose face
+ * neighbour lives on another rank reads that neighbour's projection from the halo block
+ * (mesh->n_halo slots, BT x 9 values each in the contraction type, laid out
+ * [slot][quantity][BT]).  Per step: yt_step_phase(0); yt_solver_halo_pack (gathers the
+ * projections that other ranks need, in the order of the send list); the transfer
+ * (NCCL, peer copies or host staging: the caller's) into yt_solver_halo_buffer;
+ * yt_step_phase_tiles(1) on the tiles without remote neighbours may run while it is in
+ * flight; then phase 1 on the other tiles.  Elastic YT_F64 / YT_F32 solvers only. */
+/* Sets the send list: n_pairs (local element, face j) pairs (host, int32 x 2 each). */
+yt_status yt_solver_set_send_list(struct yt_solver* solver, const int32_t* pairs, int64_t n_pairs);
+/* Gathers the projections of the send list (after phase 0) into `out` (device,
+ * n_pairs x 9 x BT values of the contraction type), on `stream`. */
+yt_status yt_solver_halo_pack(struct yt_solver* solver, void* out, yt_stream stream);
+/* Device address and size in bytes of the halo block (receive into it before phase 1). */
+yt_status yt_solver_halo_buffer(struct yt_solver* solver, void** ptr, int64_t* bytes);
+/* Copies n_halo x 9 x BT values (device memory, contraction type) into the halo block on
+ * `stream` (for receive buffers that the caller owns). */
+yt_status yt_solver_halo_unpack(struct yt_solver* solver, const void* in, yt_stream stream);
+/* One phase (0 or 1, as yt_step_phase) of the fused step over tiles [tile0, tile0 + n)
+ * (tiles of 32 consecutive elements); phase 1 of a tile needs phase 0 of every tile and
+ * the halo.  The number of tiles is ceil(E / 32). */
+yt_status yt_step_phase_tiles(struct yt_solver* solver, int32_t phase, int64_t tile0, int64_t n_tiles,
+                              yt_stream stream);
+
 /* Flops per element executed by the two phases of yt_step, and their algorithmic device
  * bytes per element (each stream read or written once). */
 yt_status yt_solver_stats(const struct yt_solver* solver, double* local_flops,

@@ -30,7 +30,7 @@ class MeshDesc(C.Structure):
     _fields_ = [("n_elements", C.c_int64), ("material", C.POINTER(C.c_double)),
                 ("jacobian", C.POINTER(C.c_double)), ("neighbours", C.POINTER(C.c_int32)),
                 ("faces", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8)),
-                ("attenuation", C.POINTER(C.c_double))]
+                ("attenuation", C.POINTER(C.c_double)), ("n_halo", C.c_int64)]
 
 
 class SchemeDesc(C.Structure):
@@ -78,6 +78,11 @@ SIGNATURES = {
     "yt_solver_status": (C.c_int, [_P, _P]),
     "yt_solver_reference_matrix": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "yt_solver_destroy": (None, [_P]),
+    "yt_solver_set_send_list": (C.c_int, [_P, C.POINTER(C.c_int32), C.c_int64]),
+    "yt_solver_halo_pack": (C.c_int, [_P, _P, _P]),
+    "yt_solver_halo_buffer": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64)]),
+    "yt_solver_halo_unpack": (C.c_int, [_P, _P, _P]),
+    "yt_step_phase_tiles": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int64, _P]),
     "yt_batch_create": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(C.c_int8), C.POINTER(SchemeDesc), _P, C.POINTER(_P)]),
     "yt_batch_set_dofs": (C.c_int, [_P, _P, C.c_int, _P]),
     "yt_batch_get": (C.c_int, [_P, C.c_int, _P, C.c_int, _P]),

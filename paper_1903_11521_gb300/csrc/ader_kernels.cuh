@@ -461,7 +461,9 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const double* Qt = Q + tile * (NQT * B * kTile);
-  double* It = Iout + tile * (NQT * B * kTile);
+  // VE: this tile's I, read and accumulated during the derivatives (the elastic path
+  // forms its pointer only where it publishes I, so nothing extra lives through the CK)
+  double* Ive = VE ? Iout + tile * (NQT * B * kTile) : nullptr;
 
   // star coefficients of row p = w
   const int s0 = SP.start[w], cnt = SP.start[w + 1] - s0;
@@ -488,7 +490,7 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
       for (int l = 0; l < 3; ++l) om[l] = __ldg(V.om + (tile * 3 + l) * kTile + lane);
       Real* th = V.theta + ((tile * kNTheta + w) * B) * kTile + lane;
       const double* qth = Qt + ((size_t)(9 + w) * B) * kTile + lane;
-      double* ith = It + ((size_t)(9 + w) * B) * kTile + lane;
+      double* ith = Ive + ((size_t)(9 + w) * B) * kTile + lane;
       for (int k = 0; k < B; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
@@ -496,7 +498,7 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
           th[l * LS + k * kTile] = from_f64<Real, CVT>(q);
           ith[l * LS + k * kTile] = dt * T.invfact[0] * q;
         }
-      for (int k = NI; k < B; ++k) It[((size_t)w * B + k) * kTile + lane] = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+      for (int k = NI; k < B; ++k) Ive[((size_t)w * B + k) * kTile + lane] = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
     }
   }
 #pragma unroll
@@ -512,10 +514,11 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
   }
   // (own column only is read before the first barrier)
   const Real* xcol = Dsh + w * kTile + lane;      // this thread's shared operand rows
-  if constexpr (VE) ck_ve<N, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Ish, w, lane, V, tile, s0, om, It);
+  if constexpr (VE) ck_ve<N, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Ish, w, lane, V, tile, s0, om, Ive);
   else ck_step<N, 0, Real, RS, SD>(T, dt, scol, cnt, Dsh, D, Xsh, sc, Icol, Ish, w, lane);
 
   // publish I: operand column (own) and HBM
+  double* It = Iout + tile * (NQT * B * kTile);
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     double ik;
@@ -561,14 +564,16 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
 #pragma unroll
           for (int s = 0; s < 3; ++s)
             if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
-        double src = 0.0;                        // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
         if constexpr (VE) {
+          double src = 0.0;                      // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
           if (w < 6) {
             const double* ith = It + ((size_t)(9 + w) * B + k) * kTile + lane;
             src = -((ith[0] + ith[(size_t)6 * B * kTile]) + ith[(size_t)12 * B * kTile]);
           }
+          Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v) + src;
+        } else {
+          Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v);
         }
-        Qo[(w * B + k) * kTile + lane] = Qt[(w * B + k) * kTile + lane] + to_f64<Real, CVT>(v) + src;
       }
     });
     __syncthreads();

@@ -350,6 +350,8 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.groups = FaceGroups{};
   L.groups.base[0] = s->Pface;
   L.groups.bt[0] = s->BT;
+  L.groups.base[1] = s->halo;      // partitioned solves: remote face projections
+  L.groups.bt[1] = s->BT;
   const bool f32 = s->prec != YT_F64;
   L.val = f32 ? (const void*)s->d_val32 : (const void*)s->d_val;
   L.f = f32 ? (const void*)s->d_f32 : (const void*)s->d_f;
@@ -734,6 +736,9 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     YT_REQUIRE(!ve || scheme->precision == YT_F64 || scheme->precision == YT_F32, YT_ERR_UNSUPPORTED,
                "27-quantity solvers: YT_F64 or YT_F32");
     YT_REQUIRE(!ve || nb, YT_ERR_INVALID, "27-quantity solvers need the face connectivity");
+    YT_REQUIRE(mesh->n_halo >= 0 && mesh->n_halo < (int64_t(1) << 26), YT_ERR_INVALID, "n_halo out of range");
+    YT_REQUIRE(mesh->n_halo == 0 || (nb && !ve && scheme->precision != YT_BF16X3_F32ACC), YT_ERR_UNSUPPORTED,
+               "partitioned solves: elastic YT_F64 / YT_F32 with connectivity");
     auto s = std::make_unique<yt_solver>();
     s->alloc_async = t_alloc.async;
     s->alloc_stream = t_alloc.stream;
@@ -756,9 +761,17 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
         for (int f = 0; f < 4; ++f) {
           const int64_t n = mesh->neighbours[e * 4 + f];
           const int j = mesh->faces[e * 4 + f], h = mesh->orient[e * 4 + f];
-          YT_REQUIRE(n >= 0 && n < s->E, YT_ERR_INVALID, "neighbour index out of range");
           YT_REQUIRE(j >= 0 && j < 4 && h >= 0 && h < 3, YT_ERR_INVALID, "face/orientation out of range");
-          conn[e * 4 + f] = (int)((n << 7) | (j << 2) | h);
+          if (n < 0) {
+            // halo slot t = -1 - n: group 1, addressed as element t / 4, face t % 4 (the
+            // block [slot][9][BT] is then read at ((t/4) * 4 + t%4) * 9 * BT = t * 9 * BT)
+            const int64_t t = -1 - n;
+            YT_REQUIRE(t < mesh->n_halo, YT_ERR_INVALID, "halo slot out of range");
+            conn[e * 4 + f] = (int)(((t >> 2) << 7) | (1 << 4) | ((t & 3) << 2) | h);
+          } else {
+            YT_REQUIRE(n < s->E, YT_ERR_INVALID, "neighbour index out of range");
+            conn[e * 4 + f] = (int)((n << 7) | (j << 2) | h);
+          }
         }
     }
     build_tables(s.get());
@@ -780,6 +793,11 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     const size_t pbytes = (size_t)s->Epad * 4 * kNq *
                           (s->prec == YT_BF16X3_F32ACC ? (size_t)tc::up8(s->BT) : (size_t)s->BT) * s->real_bytes;
     s->Pface = dalloc<unsigned char>(pbytes);
+    s->n_halo = mesh->n_halo;
+    if (s->n_halo > 0) {
+      s->halo = dalloc<unsigned char>((size_t)s->n_halo * kNq * s->BT * s->real_bytes);
+      cuda_check(cudaMemsetAsync(s->halo, 0, (size_t)s->n_halo * kNq * s->BT * s->real_bytes, st), "memset halo");
+    }
     s->Wloc = dalloc<unsigned char>((size_t)s->Epad * 4 * kNq * s->BT * s->real_bytes);
     s->star = dalloc<double>((size_t)s->Epad * 3 * kStarSlots);
     s->floc = dalloc<double>((size_t)s->Epad * 4 * 81);
@@ -1005,6 +1023,81 @@ extern "C" yt_status yt_step_host(yt_solver* s, const double* dofs_in, double* d
     }
     cuda_check(cudaEventRecord(s->ev_done, cp), "event record");
     cuda_check(cudaStreamWaitEvent(st, s->ev_done, 0), "stream wait");
+  });
+}
+
+namespace {
+// out[(i * 9 + q) * BT + m] = Pface[((le_i * 4 + j_i) * 9 + q) * BT + m]
+template <typename Real>
+__global__ void k_halo_pack(const Real* __restrict__ P, const int* __restrict__ pairs, Real* __restrict__ out,
+                            int64_t n, int BT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kNq * BT) return;
+  const int64_t pair = i / (kNq * BT);
+  const int64_t r = i % (kNq * BT);
+  out[i] = P[((int64_t)pairs[2 * pair] * 4 + pairs[2 * pair + 1]) * kNq * BT + r];
+}
+}  // namespace
+
+extern "C" yt_status yt_solver_set_send_list(yt_solver* s, const int32_t* pairs, int64_t n) {
+  return guarded([&] {
+    YT_REQUIRE(s && (pairs || n == 0) && n >= 0, YT_ERR_INVALID, "null argument");
+    YT_REQUIRE(s->P == kNq && s->prec != YT_BF16X3_F32ACC, YT_ERR_UNSUPPORTED,
+               "partitioned solves: elastic YT_F64 / YT_F32");
+    for (int64_t i = 0; i < n; ++i)
+      YT_REQUIRE(pairs[2 * i] >= 0 && pairs[2 * i] < s->E && pairs[2 * i + 1] >= 0 && pairs[2 * i + 1] < 4,
+                 YT_ERR_INVALID, "send pair out of range");
+    if (s->d_send) s->free_device(s->d_send);
+    s->d_send = nullptr;
+    s->n_send = n;
+    if (n > 0) {
+      s->d_send = sdalloc<int>(s, (size_t)(2 * n));
+      cuda_check(cudaMemcpy(s->d_send, pairs, (size_t)(2 * n) * sizeof(int), cudaMemcpyHostToDevice), "copy send list");
+    }
+  });
+}
+
+extern "C" yt_status yt_solver_halo_pack(yt_solver* s, void* out, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s && (out || s->n_send == 0), YT_ERR_INVALID, "null argument");
+    if (s->n_send == 0) return;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t total = s->n_send * kNq * s->BT;
+    if (s->prec == YT_F64)
+      k_halo_pack<double><<<blocks_for(total, 256), 256, 0, st>>>(static_cast<const double*>(s->Pface), s->d_send,
+                                                                  static_cast<double*>(out), s->n_send, s->BT);
+    else
+      k_halo_pack<float><<<blocks_for(total, 256), 256, 0, st>>>(static_cast<const float*>(s->Pface), s->d_send,
+                                                                 static_cast<float*>(out), s->n_send, s->BT);
+    cuda_check(cudaGetLastError(), "k_halo_pack");
+  });
+}
+
+extern "C" yt_status yt_solver_halo_buffer(yt_solver* s, void** ptr, int64_t* bytes) {
+  return guarded([&] {
+    YT_REQUIRE(s && ptr, YT_ERR_INVALID, "null argument");
+    *ptr = s->halo;
+    if (bytes) *bytes = s->n_halo * kNq * s->BT * (int64_t)s->real_bytes;
+  });
+}
+
+extern "C" yt_status yt_solver_halo_unpack(yt_solver* s, const void* in, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s && (in || s->n_halo == 0), YT_ERR_INVALID, "null argument");
+    if (s->n_halo == 0) return;
+    cuda_check(cudaMemcpyAsync(s->halo, in, (size_t)s->n_halo * kNq * s->BT * s->real_bytes,
+                               cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)), "halo unpack");
+  });
+}
+
+extern "C" yt_status yt_step_phase_tiles(yt_solver* s, int32_t phase, int64_t t0, int64_t nt, yt_stream stream) {
+  return guarded([&] {
+    YT_REQUIRE(s, YT_ERR_INVALID, "null solver");
+    YT_REQUIRE(phase == 0 || phase == 1, YT_ERR_INVALID, "phase must be 0 or 1");
+    YT_REQUIRE(s->has_neighbours, YT_ERR_INVALID, "solver was created without neighbours");
+    YT_REQUIRE(t0 >= 0 && nt >= 0 && t0 + nt <= s->ntiles, YT_ERR_INVALID, "tile range out of range");
+    if (nt == 0) return;
+    dispatch_chunk(s, reinterpret_cast<cudaStream_t>(stream), phase, t0, nt);
   });
 }
 

@@ -42,6 +42,11 @@ struct yt_solver {
   double *cth = nullptr, *om = nullptr, *fthl = nullptr, *fthn = nullptr;
   void *cth_r = nullptr, *om_r = nullptr, *fthl_r = nullptr, *fthn_r = nullptr, *theta = nullptr;
   size_t smem_theta = 0;
+  // partitioned solves: halo block [n_halo][9][BT] (contraction type, group 1 of the
+  // neighbour gathers) and the send list
+  int64_t n_halo = 0, n_send = 0;
+  void* halo = nullptr;
+  int* d_send = nullptr;
   // device memory from the stream-ordered allocator on alloc_stream (solvers of a server),
   // else from cudaMalloc
   bool alloc_async = false;
@@ -58,7 +63,8 @@ struct yt_solver {
   ~yt_solver() {
     if (star_r == (void*)star) star_r = floc_r = fnb_r = nullptr;
     if (cth_r == (void*)cth) cth_r = om_r = fthl_r = fthn_r = nullptr;
-    for (void* p : {(void*)cth, (void*)om, (void*)fthl, (void*)fthn, cth_r, om_r, fthl_r, fthn_r, theta})
+    for (void* p : {(void*)cth, (void*)om, (void*)fthl, (void*)fthn, cth_r, om_r, fthl_r, fthn_r, theta,
+                    halo, (void*)d_send})
       free_device(p);
     for (cudaEvent_t e : ev_in) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_out) if (e) cudaEventDestroy(e);

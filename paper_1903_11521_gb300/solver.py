@@ -28,7 +28,7 @@ class Solver:
     or None.  DOFs are exchanged in the canonical layout [element][quantity][basis]."""
 
     def __init__(self, order, dt, material, jacobian, neighbours=None, faces=None,
-                 orient=None, precision=_lib.YT_F64, stream=None, flags=0, attenuation=None):
+                 orient=None, precision=_lib.YT_F64, stream=None, flags=0, attenuation=None, n_halo=0):
         """attenuation: None (elastic, 9 quantities) or an object with (E, 3) arrays
         omega, ylam, ymu of the three mechanisms (27 quantities)."""
         self.lib = _lib.load()
@@ -50,6 +50,7 @@ class Solver:
             desc.neighbours = _ptr(self._nb, C.c_int32)
             desc.faces = _ptr(self._fj, C.c_int8)
             desc.orient = _ptr(self._fh, C.c_int8)
+        desc.n_halo = int(n_halo)
         self.n_quantities = 9
         if attenuation is not None:
             self._att = np.ascontiguousarray(np.stack([attenuation.omega, attenuation.ylam,
@@ -121,6 +122,24 @@ class Solver:
 
     def step_phase(self, phase: int, stream=None):
         _lib.check(self.lib.yt_step_phase(self.handle, phase, _stream_handle(stream)), "yt_step_phase")
+
+    def step_phase_tiles(self, phase: int, tile0: int, n_tiles: int, stream=None):
+        _lib.check(self.lib.yt_step_phase_tiles(self.handle, phase, int(tile0), int(n_tiles),
+                                                _stream_handle(stream)), "yt_step_phase_tiles")
+
+    def set_send_list(self, pairs):
+        """pairs: (n, 2) int (local element, face j) whose projections other ranks need."""
+        self._send = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        _lib.check(self.lib.yt_solver_set_send_list(self.handle, _ptr(self._send, C.c_int32),
+                                                    self._send.shape[0]), "yt_solver_set_send_list")
+
+    def halo_pack(self, out_ptr: int, stream=None):
+        _lib.check(self.lib.yt_solver_halo_pack(self.handle, out_ptr, _stream_handle(stream)),
+                   "yt_solver_halo_pack")
+
+    def halo_unpack(self, in_ptr: int, stream=None):
+        _lib.check(self.lib.yt_solver_halo_unpack(self.handle, in_ptr, _stream_handle(stream)),
+                   "yt_solver_halo_unpack")
 
     def status(self, stream=None):
         """Synchronises the stream; raises YtError (YT_ERR_TIMEOUT) if a bounded

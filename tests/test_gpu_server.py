@@ -44,8 +44,8 @@ def test_mix_equals_alone_and_budget_respected(yt):
     reqs = []
     for i in range(10):
         order = int(rng.integers(3, 7))
-        E = int(rng.integers(200, 5000))
-        steps = int(rng.integers(3, 9))
+        E = int(rng.integers(2000, 8000))
+        steps = int(rng.integers(40, 80))     # long enough that solves overlap in time
         reqs.append((make_request(1000 + 10 * i, order, E), steps))
     budget = 400 * 2 ** 20          # about half of the ten requests at once
     srv = yt.Server(budget, precision=yt.YT_F32)
