@@ -45,8 +45,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_local per element,
 # from one capture of a 40,000-tet case per order, keyed by the sha256 prefix of the
 # kernel source it was captured on
-NCU_TRAFFIC_PER_ELEMENT = {"195bc11c65083de9": {6: (302.036736e6 + 752.325376e6) / 40000},
-                           "9a62b690f3f24716": {7: (411.281e6 + 1203.183e6) / 40000}}
+NCU_TRAFFIC_PER_ELEMENT = {"2cafbc2980c268b0": {6: (303.201280e6 + 752.416512e6) / 40000},
+                           "1dcde163dd8458e4": {7: (410.703616e6 + 1193.518080e6) / 40000}}
 
 
 def kernel_source_digest(order=6, precision="f64"):

@@ -55,7 +55,7 @@ typedef enum yt_precision {
                               operand split into two bfloat16 parts (hi + lo), three
                               products hi*hi + hi*lo + lo*hi accumulated in binary32;
                               per-element 9x9 products in binary32, DOFs and time-integral
-                              accumulation in binary64 (solver only, orders 2..6) */
+                              accumulation in binary64 (solver only, orders 2..7) */
 } yt_precision;
 
 typedef enum yt_memory { YT_MEM_HOST = 0, YT_MEM_DEVICE = 1 } yt_memory;
@@ -189,7 +189,7 @@ typedef struct yt_mesh_desc {
 typedef struct yt_scheme_desc {
   int32_t order;             /* convergence order O = N + 1: 2..7 */
   double dt;                 /* time step */
-  yt_precision precision;    /* YT_F64 or YT_F32 (orders 2..7), YT_BF16X3_F32ACC (2..6) */
+  yt_precision precision;    /* YT_F64, YT_F32 or YT_BF16X3_F32ACC (orders 2..7) */
   int32_t flags;             /* 0, or YT_SCHEME_DIAG_EXPIRE_WAIT */
   int32_t quantities;        /* 9 (or 0): elastic; 27: viscoelastic-shaped (below) */
 } yt_scheme_desc;
@@ -391,8 +391,10 @@ void yt_server_destroy(struct yt_server* server);
 yt_status yt_server_fail_tick(struct yt_server* server, int64_t at_tick);
 
 /* Host-only diagnostics: the global-matrix operands of the tensor-core kernels of an order
- * (2..6) as uploaded by a YT_BF16X3_F32ACC solver; kernel 0 = the local kernel (passes:
- * CK derivatives, volume chunks, face projections), 1 = the neighbour kernel (lifting).
+ * (2..7) as uploaded by a YT_BF16X3_F32ACC solver; kernel 0 = the local kernel (passes:
+ * CK derivatives -- at order 7 the first derivative as two passes over its output rows
+ * [0, 32) and [32, 56) --, volume chunks, face projections), 1 = the neighbour kernel
+ * (lifting).
  * Each pass is an N x K matrix stored twice (bf16 hi parts, then lo parts) in the
  * K-major canonical layout of 8 x 8 core matrices: entry (n, k) at byte
  * (n/8)*16K + (k/8)*128 + (n%8)*16 + (k%8)*2.  `bytes` receives the size; pass out == NULL

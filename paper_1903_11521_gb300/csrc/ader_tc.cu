@@ -1,6 +1,6 @@
 // Host side of the tensor-core step (precision YT_BF16X3_F32ACC): the split-bf16 global
 // matrices in the kernels' canonical shared-memory layout, kernel attributes and
-// launches for degrees N = 1..5.
+// launches for degrees N = 1..6.
 #include <cstring>
 #include <vector>
 
@@ -40,20 +40,22 @@ void operands_local(std::vector<unsigned char>& out) {
   const RefMatrices& R = reference_matrices(N);
   const int B = R.B, BT = R.BT;
   out.assign(L::BLOB, 0);
-  // CK derivative delta: Ktilde^x restricted to the staircase (rows < nd(delta+1),
-  // columns < nd(delta), as in the sparse kernels)
-  for (int d = 0; d < N; ++d) {
-    const int nin = Dims<N>::nd(d), nout = Dims<N>::nd(d + 1), r8 = L::r8(d);
+  // CK derivative passes: Ktilde^x of derivative delta restricted to the staircase (rows
+  // < nd(delta+1), columns < nd(delta), as in the sparse kernels), each pass holding its
+  // block of output rows [row0, row0 + rows) at columns x * r8 + k - row0
+  for (int p = 0; p < L::ND; ++p) {
+    const int d = tc::tc_delta<N>(p), row0 = tc::tc_row0<N>(p), rows = tc::tc_rows<N>(p);
+    const int nin = Dims<N>::nd(d), r8 = L::r8(p);
     for (int x = 0; x < 3; ++x)
-      for (int k = 0; k < nout; ++k)
+      for (int k = row0; k < row0 + rows; ++k)
         for (int l = 0; l < nin; ++l) {
           const double v = R.Ktilde[(size_t)x * B * B + k + (size_t)l * B];
-          if (v != 0.0) put_split(out, L::off(d), L::np(d), L::kp(d), x * r8 + k, l, v);
+          if (v != 0.0) put_split(out, L::off(p), L::np(p), L::kp(p), x * r8 + (k - row0), l, v);
         }
   }
   // volume: Khat^x, columns l < C(N+2,3) (the others are zero: equivalent sparsity)
   for (int v = 0; v < L::NV; ++v) {
-    const int p = N + v, k0 = v * L::VR, r8 = L::r8(p);
+    const int p = L::ND + v, k0 = v * L::VR, r8 = L::r8(p);
     for (int x = 0; x < 3; ++x)
       for (int k = k0; k < k0 + L::vrows(v); ++k)
         for (int l = 0; l < B; ++l) {
@@ -64,7 +66,7 @@ void operands_local(std::vector<unsigned char>& out) {
         }
   }
   // face projections R^sT: column s * BT8 + m, K = l
-  const int pp = N + L::NV;
+  const int pp = L::ND + L::NV;
   for (int s = 0; s < 4; ++s)
     for (int m = 0; m < BT; ++m)
       for (int l = 0; l < B; ++l) {
@@ -139,7 +141,8 @@ void launch_neigh(const tc::TcLaunch& L, int variant) {
     case 3: CALL(3); break;                                                    \
     case 4: CALL(4); break;                                                    \
     case 5: CALL(5); break;                                                    \
-    default: throw Error(YT_ERR_UNSUPPORTED, "tensor-core step: orders 2..6"); \
+    case 6: CALL(6); break;                                                    \
+    default: throw Error(YT_ERR_UNSUPPORTED, "tensor-core step: orders 2..7"); \
   }
 
 size_t tc_smem_local(int N) {
@@ -195,7 +198,7 @@ void tc_launch_neigh(int N, const tc::TcLaunch& L, int variant) {
 extern "C" yt_status yt_tc_operands(int32_t order, int32_t kernel, unsigned char* out, int64_t* bytes) {
   return yt::guarded([&] {
     YT_REQUIRE(bytes, YT_ERR_INVALID, "null argument");
-    YT_REQUIRE(order >= 2 && order <= 6, YT_ERR_UNSUPPORTED, "tensor-core operands: orders 2..6");
+    YT_REQUIRE(order >= 2 && order <= 7, YT_ERR_UNSUPPORTED, "tensor-core operands: orders 2..7");
     YT_REQUIRE(kernel == 0 || kernel == 1, YT_ERR_INVALID, "kernel must be 0 (local) or 1 (neighbour)");
     std::vector<unsigned char> v;
     if (kernel == 0) yt::tc_operands_local(order - 1, v);

@@ -60,10 +60,28 @@ __host__ __device__ constexpr int group_first_row(int g) { return g == 0 ? 32 : 
 __host__ __device__ constexpr int group_of(int q) { return q < 4 ? 0 : (q < 8 ? 1 : 2); }
 
 // Passes of the two kernels of degree N.  A pass is one set of MMAs into the three
-// accumulator groups (N columns each, K = kp): k_local runs CK derivatives delta = 0..N-1
-// (columns x * R8 + k, R = C(N-delta+2,3) output rows), NV volume passes over row chunks
+// accumulator groups (N columns each, K = kp): k_local runs the CK derivatives (columns
+// x * R8 + k - row0 for the output rows k of the pass), NV volume passes over row chunks
 // (columns x * R8 + k - k0) and the face projections (columns s * BT8 + m); k_neigh runs
-// one lifting pass (columns k, K = s * BT8 + m).
+// the lifting (columns k, K = s * BT8 + m).  When the first derivative's three directions
+// would need more than 160 accumulator columns per group (order 7: 3 x 56), it runs as
+// two passes over its rows [0, 32) and [32, C(N+2,3)): derivative passes p < ND, with
+// derivative tc_delta(p), first row tc_row0(p) and tc_rows(p) rows.
+constexpr int kSplitRows = 32;
+template <int N>
+__host__ __device__ constexpr bool tc_split0() { return 3 * up8(Dims<N>::nd(1)) > 160; }
+template <int N>
+__host__ __device__ constexpr int tc_nderiv() { return N + (tc_split0<N>() ? 1 : 0); }
+template <int N>
+__host__ __device__ constexpr int tc_delta(int p) { return tc_split0<N>() ? (p == 0 ? 0 : p - 1) : p; }
+template <int N>
+__host__ __device__ constexpr int tc_row0(int p) { return (tc_split0<N>() && p == 1) ? kSplitRows : 0; }
+template <int N>
+__host__ __device__ constexpr int tc_rows(int p) {
+  return (tc_split0<N>() && p == 0) ? kSplitRows
+                                    : ((tc_split0<N>() && p == 1) ? Dims<N>::nd(1) - kSplitRows
+                                                                  : Dims<N>::nd(tc_delta<N>(p) + 1));
+}
 template <int N>
 __host__ __device__ constexpr int tc_nv() {
   int n = 1;
@@ -78,26 +96,35 @@ __host__ __device__ constexpr int tc_vrows(int v) {
 }
 template <int N>
 __host__ __device__ constexpr int tc_r8(int p) {
-  return p < N ? up8(Dims<N>::nd(p + 1)) : (p < N + tc_nv<N>() ? up8(tc_vrows<N>(p - N)) : up8(Dims<N>::BT));
+  return p < tc_nderiv<N>() ? up8(tc_rows<N>(p))
+                            : (p < tc_nderiv<N>() + tc_nv<N>() ? up8(tc_vrows<N>(p - tc_nderiv<N>())) : up8(Dims<N>::BT));
 }
 template <int N>
 __host__ __device__ constexpr int tc_np(int p) {
-  return p < N + tc_nv<N>() ? up16(3 * tc_r8<N>(p)) : up16(4 * up8(Dims<N>::BT));
+  return p < tc_nderiv<N>() + tc_nv<N>() ? up16(3 * tc_r8<N>(p)) : up16(4 * up8(Dims<N>::BT));
 }
 template <int N>
 __host__ __device__ constexpr int tc_kp(int p) {
-  return p < N ? up16(Dims<N>::nd(p)) : (p < N + tc_nv<N>() ? up16(Dims<N>::nd(1)) : up16(Dims<N>::B));
+  return p < tc_nderiv<N>() ? up16(Dims<N>::nd(tc_delta<N>(p)))
+                            : (p < tc_nderiv<N>() + tc_nv<N>() ? up16(Dims<N>::nd(1)) : up16(Dims<N>::B));
 }
 template <int N>
-__host__ __device__ constexpr int tc_off(int p) {
-  return p == 0 ? 0 : tc_off<N>(p - 1) + 2 * tc_np<N>(p - 1) * tc_kp<N>(p - 1) * 2;
-}
+__host__ __device__ constexpr int tc_size(int p) { return 2 * tc_np<N>(p) * tc_kp<N>(p) * 2; }
+template <int N>
+__host__ __device__ constexpr int tc_off(int p) { return p == 0 ? 0 : tc_off<N>(p - 1) + tc_size<N>(p - 1); }
 template <int N>
 __host__ __device__ constexpr int tc_cs() {
   int c = 0;
-  for (int p = 0; p < N + tc_nv<N>() + 1; ++p) c = max2(c, tc_np<N>(p));
+  for (int p = 0; p < tc_nderiv<N>() + tc_nv<N>() + 1; ++p) c = max2(c, tc_np<N>(p));
   return c;
 }
+template <int N>
+__host__ __device__ constexpr int tc_pass_max() {
+  int c = 0;
+  for (int p = 0; p < tc_nderiv<N>() + tc_nv<N>() + 1; ++p) c = max2(c, tc_size<N>(p));
+  return c;
+}
+constexpr size_t kSmemCap = 232448;      // dynamic shared memory of one CTA (227 KB)
 
 // first scratch row of D~^d (d >= 1): rows C(N-d+3,3) of every earlier derivative
 template <int N>
@@ -110,31 +137,49 @@ struct Layout {
   static constexpr int KPA = up16(B);                  // K capacity, k_local element operand
   static constexpr int NV = tc_nv<N>();
   static constexpr int VR = tc_vr<N>();               // rows per volume pass
-  static constexpr int NPASS = N + NV + 1;
+  static constexpr bool SPLIT0 = tc_split0<N>();
+  static constexpr int ND = tc_nderiv<N>();            // derivative passes
+  static constexpr int NPASS = ND + NV + 1;
   __host__ __device__ static constexpr int vrows(int v) { return tc_vrows<N>(v); }
   __host__ __device__ static constexpr int r8(int p) { return tc_r8<N>(p); }
   __host__ __device__ static constexpr int np(int p) { return tc_np<N>(p); }
   __host__ __device__ static constexpr int kp(int p) { return tc_kp<N>(p); }
   __host__ __device__ static constexpr int off(int p) { return tc_off<N>(p); }
+  __host__ __device__ static constexpr int size(int p) { return tc_size<N>(p); }
   static constexpr int BLOB = tc_off<N>(NPASS);
   static constexpr int CS = tc_cs<N>();               // TMEM columns per group
   // rows of the scaled derivatives D~^1..D~^N kept for the time integral (per-CTA scratch)
   static constexpr int SROWS = tc_srow<N>(N + 1);
   static constexpr int OPA_SPLIT = kRows * KPA * 2;    // bytes of one split
-  static constexpr int XS_FLOATS = 3 * kNq * 2 * kTile * 4;
-  static constexpr size_t SMEM = (size_t)2 * OPA_SPLIT + BLOB + XS_FLOATS * 4 + 64;
-  // k_neigh
-  static constexpr int KPN = up16(4 * BT8);
+  // exchange buffer: 3 directions (mixing) or BT8 / 8 chunks (face projections) of
+  // [9][2][32][4] floats
+  static constexpr int XS_CHUNKS = max2(3, BT8 / 8);
+  static constexpr int XS_FLOATS = XS_CHUNKS * kNq * 2 * kTile * 4;
+  // the global-matrix operands of all passes stay in shared memory when they fit beside
+  // the element operand; otherwise (order 7) each pass's operand is loaded into one
+  // buffer while the previous pass's accumulators are mixed (STREAM)
+  static constexpr bool STREAM = (size_t)2 * OPA_SPLIT + BLOB + XS_FLOATS * 4 + 64 > kSmemCap;
+  static constexpr int OPB_BYTES = STREAM ? tc_pass_max<N>() : BLOB;
+  static constexpr size_t SMEM = (size_t)2 * OPA_SPLIT + OPB_BYTES + XS_FLOATS * 4 + 64;
+  // k_neigh: the lifting with K = the four faces' W stacked, or (order 7, LIFT2) two
+  // passes of two faces each (K = 2 BT8), accumulated in tensor memory, so that the
+  // element operand holds two faces only
+  static constexpr int KPN = up16(4 * BT8);            // K of the Rhat operand (all faces)
   static constexpr int NPL = up16(B);
-  static constexpr int OPN_SPLIT = kRows * KPN * 2;
   static constexpr int BLOB_N = 2 * NPL * KPN * 2;
   static constexpr int STAGE_FLOATS = BT8 * kNq * kTile;     // one face of gathered projections
-  static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 3 * STAGE_FLOATS * 4 + 64;
+  static constexpr bool LIFT2 = (size_t)2 * kRows * KPN * 2 + BLOB_N + 3 * STAGE_FLOATS * 4 + 64 > kSmemCap;
+  static constexpr int KPE = LIFT2 ? up16(2 * BT8) : KPN;      // K of the element operand
+  static constexpr int OPN_SPLIT = kRows * KPE * 2;
+  static constexpr int XSN_FLOATS = LIFT2 ? (BT + 3) / 4 * 4 * kNq * kTile : STAGE_FLOATS;
+  static constexpr size_t SMEM_N = (size_t)2 * OPN_SPLIT + BLOB_N + 2 * STAGE_FLOATS * 4 + XSN_FLOATS * 4 + 64;
   // k_local_tc converts with the integer units (fp_convert.cuh) except at degree 5, where
   // the extra registers cost more than the FP64-pipe slots they save (measured)
   static constexpr bool INT_CVT_LOCAL = N <= 4;
   static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
-  static_assert(BT8 / 8 <= 3, "face basis too large for the exchange buffer");
+  static_assert(BT8 / 8 <= XS_CHUNKS, "face basis too large for the exchange buffer");
+  static_assert(SMEM <= kSmemCap && SMEM_N <= kSmemCap, "shared memory of one CTA exceeded");
+  static_assert(!SPLIT0 || (kSplitRows % 8 == 0 && NI > kSplitRows), "split of the first derivative");
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -268,21 +313,30 @@ __device__ __forceinline__ void store_split8(unsigned char* op, int split_bytes,
 // independent and issue in parallel) and committed to `bar` (expected count 3).  The
 // descriptors of step j differ from step 0 only in the start address (+256 B, i.e. +16
 // in the address field, which cannot carry: shared addresses are below 256 KB).
-__device__ __forceinline__ void issue_group(int g, uint32_t tmem, int cs, uint32_t a_base, int a_split,
-                                            int kpa, uint32_t b_base, int np, int kp, uint32_t bar) {
+// The MMAs of accumulator group g over `ksteps` K-steps of 16: A (element operand, K
+// capacity kpa, lo part a_split bytes after hi), B (global-matrix operand, K capacity kpb
+// for its row-group stride, lo part b_split bytes after hi; b_base may point into its
+// K range).  The first product starts the accumulator unless `acc` (continue it).
+__device__ __forceinline__ void issue_group_k(int g, uint32_t tmem, int cs, uint32_t a_base, int a_split,
+                                              int kpa, uint32_t b_base, int b_split, int np, int kpb,
+                                              int ksteps, bool acc, uint32_t bar) {
   const uint32_t idesc = idesc_bf16(np);
-  const uint32_t sbo_a = (uint32_t)kpa * 16, sbo_b = (uint32_t)kp * 16;
+  const uint32_t sbo_a = (uint32_t)kpa * 16, sbo_b = (uint32_t)kpb * 16;
   const uint32_t a_hi = a_base + (uint32_t)(group_first_row(g) / 8) * sbo_a;
   const uint64_t dah = smem_desc(a_hi, sbo_a), dal = smem_desc(a_hi + (uint32_t)a_split, sbo_a);
-  const uint64_t dbh = smem_desc(b_base, sbo_b), dbl = smem_desc(b_base + (uint32_t)(np * kp * 2), sbo_b);
+  const uint64_t dbh = smem_desc(b_base, sbo_b), dbl = smem_desc(b_base + (uint32_t)b_split, sbo_b);
   const uint32_t d = tmem + (uint32_t)(g * cs);
-  for (int j = 0; j < kp / 16; ++j) {
+  for (int j = 0; j < ksteps; ++j) {
     const uint64_t dk = (uint64_t)(j * 16);
-    mma_bf16(d, dah + dk, dbh + dk, idesc, j > 0);
+    mma_bf16(d, dah + dk, dbh + dk, idesc, (acc || j > 0) ? 1u : 0u);
     mma_bf16(d, dah + dk, dbl + dk, idesc, 1);
     mma_bf16(d, dal + dk, dbh + dk, idesc, 1);
   }
   mma_commit(bar);
+}
+__device__ __forceinline__ void issue_group(int g, uint32_t tmem, int cs, uint32_t a_base, int a_split,
+                                            int kpa, uint32_t b_base, int np, int kp, uint32_t bar) {
+  issue_group_k(g, tmem, cs, a_base, a_split, kpa, b_base, np * kp * 2, np, kp, kp / 16, false, bar);
 }
 
 struct TcStep {
@@ -352,7 +406,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPA
   unsigned char* opb = opa + 2 * L::OPA_SPLIT;                    // global-matrix passes
-  float* xs = reinterpret_cast<float*>(opb + L::BLOB);            // [3][9][2][32][4]
+  float* xs = reinterpret_cast<float*>(opb + L::OPB_BYTES);       // [XS_CHUNKS][9][2][32][4]
   TcShared* ts = reinterpret_cast<TcShared*>(xs + L::XS_FLOATS);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool leader = threadIdx.x == 0;
@@ -373,11 +427,14 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   fence_after_sync();
   const uint32_t tmem = ts->tmem;
   const bool issuer = lane == 0 && w < 3;          // issues accumulator group w
-  if (leader && !T.expire_first_wait) load_operands(opb, blob, L::BLOB, bar_ld);
+  // all passes' operands at once, or (STREAM) the first pass's
+  if (leader && !T.expire_first_wait) load_operands(opb, blob, L::STREAM ? L::size(0) : L::BLOB, bar_ld);
   bool ok = __syncthreads_and(tc_wait(bar_ld, 0, T.expire_first_wait ? kDiagWaitNs : kTcWaitNs)) != 0;
   uint32_t phase = 0;
   bool pending = false;              // a commit whose wait timed out
   uint32_t pending_phase = 0;
+  uint32_t ld_phase = 1;             // STREAM: phase of the next operand load
+  bool ld_out = false;               // STREAM: an operand load is in flight
 
   const uint32_t opa_s = smem_u32(opa), opb_s = smem_u32(opb);
   const int g = group_of(w);
@@ -391,14 +448,40 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   const double dt = T.dt;
   const float dtf = (float)dt;
 
-  // MMAs are issued only while ok (block-uniform), so every issued pass is waited for
-  auto issue = [&](int p) {
-    if (issuer && ok) {
-      fence_after_sync();
-      issue_group(w, tmem, CS, opa_s, L::OPA_SPLIT, KPA, opb_s + (uint32_t)L::off(p), L::np(p), L::kp(p), bar_mma);
+  // STREAM: the operand of pass p into the single operand buffer (issued only after the
+  // MMAs reading that buffer have completed), and the wait for it before the pass
+  auto load_pass = [&](int p) {
+    if constexpr (L::STREAM) {
+      if (ok) {
+        if (leader) load_operands(opb, blob + L::off(p), L::size(p), bar_ld);
+        ld_out = true;
+      }
     }
   };
-  auto wait_pass = [&]() {
+  auto pass_ready = [&]() {
+    if constexpr (L::STREAM) {
+      if (ld_out && ok) {
+        const bool all = __syncthreads_and(tc_wait(bar_ld, ld_phase)) != 0;
+        if (all) {
+          ld_phase ^= 1u;
+          ld_out = false;
+        } else {
+          ok = false;                // the final bounded wait covers the load in flight
+        }
+      }
+    }
+  };
+  // MMAs are issued only while ok (block-uniform), so every issued pass is waited for
+  auto issue = [&](int p) {
+    pass_ready();
+    if (issuer && ok) {
+      fence_after_sync();
+      issue_group(w, tmem, CS, opa_s, L::OPA_SPLIT, KPA, opb_s + (uint32_t)(L::STREAM ? 0 : L::off(p)), L::np(p),
+                  L::kp(p), bar_mma);
+    }
+  };
+  // waits for the pass in flight; STREAM: then loads the operand of pass `next` (< 0: none)
+  auto wait_pass = [&](int next) {
     const bool was_ok = ok;
     const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
     ok = __syncthreads_and(done) != 0;
@@ -408,6 +491,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
     }
     phase ^= 1u;
     fence_after_sync();
+    if (next >= 0) load_pass(next);
   };
   // publishes this thread's operand writes and TMEM reads before the next MMA issue
   auto sync_for_mma = [&]() {
@@ -482,11 +566,13 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
     sync_for_mma();
     issue(0);
 
-    // CK derivatives: D~^{delta+1} = dt sum_x (Ktilde^x D~^delta) Astar^xT, in the operand
-    static_for<0, N>([&](auto dd) {
-      constexpr int DELTA = decltype(dd)::value;
-      constexpr int R = Dm::nd(DELTA + 1), R8 = up8(R);
-      wait_pass();
+    // CK derivatives: D~^{delta+1} = dt sum_x (Ktilde^x D~^delta) Astar^xT, in the operand.
+    // Mixing of derivative pass P: its rows ROW0 + k (k < R) from accumulator columns
+    // x * R8 + k, into the scratch and (TO_OPA) the operand.
+    auto mix_deriv = [&](auto pp, auto to_opa) {
+      constexpr int P = decltype(pp)::value;
+      constexpr bool TO_OPA = decltype(to_opa)::value;
+      constexpr int DELTA = tc_delta<N>(P), R = tc_rows<N>(P), R8 = up8(R), ROW0 = tc_row0<N>(P);
       uint32_t ua[24], ub[24];       // chunk c in ua (c even) or ub (c odd)
       load_chunk(0, R8, ua);
       static_for<0, R8 / 8>([&](auto cc) {
@@ -502,19 +588,46 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
             const int k = k0 + i;
             if (k < R) {
               v[i] *= dtf;
-              my_scr[(tc_srow<N>(DELTA + 1) + k) * kRows] = v[i];
+              my_scr[(tc_srow<N>(DELTA + 1) + ROW0 + k) * kRows] = v[i];
             } else {
               v[i] = 0.0f;
             }
           }
-          store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+          if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
           if constexpr (k0 + 8 < R8) __syncthreads();
         };
         if constexpr (c % 2 == 0) body(ua, ub);
         else body(ub, ua);
       });
-      sync_for_mma();
-      if constexpr (DELTA + 1 < N) issue(DELTA + 1);
+    };
+    static_for<0, N>([&](auto dd) {
+      constexpr int DELTA = decltype(dd)::value;
+      if constexpr (L::SPLIT0 && DELTA == 0) {
+        // first derivative in two row blocks: the first block's rows go to the scratch
+        // only, since the second pass still reads D~^0 from the operand; once it is done
+        // its rows and then the first block's (from the scratch) go into the operand
+        wait_pass(1);
+        mix_deriv(std::integral_constant<int, 0>{}, std::false_type{});
+        sync_for_mma();
+        issue(1);
+        wait_pass(2 < L::ND ? 2 : L::ND);
+        mix_deriv(std::integral_constant<int, 1>{}, std::true_type{});
+        static_for<0, kSplitRows / 8>([&](auto cc) {
+          constexpr int k0 = decltype(cc)::value * 8;
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = my_scr[(tc_srow<N>(1) + k0 + i) * kRows];
+          store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+        });
+        sync_for_mma();
+        if constexpr (2 < L::ND) issue(2);
+      } else {
+        constexpr int P = DELTA + (L::SPLIT0 ? 1 : 0);   // the pass of this derivative
+        wait_pass(P + 1 < L::ND ? P + 1 : L::ND);       // then the next pass's operand
+        mix_deriv(std::integral_constant<int, P>{}, std::true_type{});
+        sync_for_mma();
+        if constexpr (P + 1 < L::ND) issue(P + 1);
+      }
     });
 
     // time integral I = sum_d (dt / (d+1)!) D~^d in binary64: HBM and operand.  All loads
@@ -550,13 +663,13 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
     });
     sync_for_mma();
-    issue(N);
+    issue(L::ND);
 
     // volume: Q[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q], row chunks of VR
     static_for<0, NV>([&](auto vv) {
       constexpr int V = decltype(vv)::value;
       constexpr int R = L::vrows(V), R8 = up8(R), KB0 = V * L::VR;
-      wait_pass();
+      wait_pass(L::ND + V + 1);       // the next volume pass or the face projections
       uint32_t ua[24], ub[24];
       double qa[8], qb[8];           // Q of chunk c in qa (c even) or qb (c odd), loaded one chunk ahead
       load_chunk(0, R8, ua);
@@ -587,8 +700,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       });
       fence_before_sync();
       __syncthreads();
-      if constexpr (V + 1 < NV) issue(N + V + 1);
-      else issue(N + NV);
+      issue(L::ND + V + 1);
     });
 
     // face projections P^s = R^sT I -> Pface; local flux products W = P^s Aloc_s^T -> Wloc
@@ -599,7 +711,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int q = 0; q < kNq; ++q) af[f][q] = __ldg(Ft + ((f * kNq + w) * kNq + q) * kTile + lane);
-    wait_pass();
+    wait_pass(tile + gridDim.x < ntiles ? 0 : -1);   // then the next tile's first operand
     float* Pe = Pface + (tile * kTile + lane) * (4 * kNq * BT8);
     float* Wt = Wloc + tile * (4 * kNq * BT * kTile);
     static_for<0, 4>([&](auto face) {
@@ -643,8 +755,10 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       __syncthreads();
     });
   }
-  // after a timeout: one more bounded wait for the pass in flight, then free
+  // after a timeout: one more bounded wait for the pass and the operand load in flight,
+  // then free
   if (pending) (void)tc_wait(bar_mma, pending_phase);
+  if (ld_out) (void)tc_wait(bar_ld, ld_phase);
   if (!ok && leader) atomicExch(status, kStatusTimeout);
   fence_before_sync();
   __syncthreads();
@@ -666,13 +780,14 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
            const float* __restrict__ fnb, const int* __restrict__ conn, const float* __restrict__ fmat,
            const unsigned char* __restrict__ blob, int64_t ntiles, int* __restrict__ status) {
   using L = Layout<N>;
-  constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPN = L::KPN, NPL = L::NPL;
+  constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPN = L::KPN, NPL = L::NPL, KPE = L::KPE;
+  constexpr int NM4 = L::LIFT2 ? (BT + 3) / 4 : BT8 / 4;        // float4 rows of the exchange
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPN
-  unsigned char* opb = opa + 2 * L::OPN_SPLIT;                    // Rhat operand
+  unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPE
+  unsigned char* opb = opa + 2 * L::OPN_SPLIT;                    // Rhat operand (K = KPN)
   float* stage = reinterpret_cast<float*>(opb + L::BLOB_N);       // 2 x [9][32][BT8] gathered
-  float* xs = stage + 2 * L::STAGE_FLOATS;                        // [BT8/4][9][32][4]
-  TcShared* ts = reinterpret_cast<TcShared*>(xs + L::STAGE_FLOATS);
+  float* xs = stage + 2 * L::STAGE_FLOATS;                        // [NM4][9][32][4]
+  TcShared* ts = reinterpret_cast<TcShared*>(xs + L::XSN_FLOATS);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool leader = threadIdx.x == 0;
   const uint32_t bar_ld = smem_u32(&ts->bar[0]), bar_mma = smem_u32(&ts->bar[1]);
@@ -702,6 +817,31 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
   const int my_row = op_row(w, lane);
   const uint32_t opa_s = smem_u32(opa), opb_s = smem_u32(opb);
 
+  // lifting pass h: faces h * FH .. of the element operand against their K range of the
+  // Rhat operand (LIFT2: two passes of two faces, the second continuing the accumulator)
+  constexpr int FH = L::LIFT2 ? 2 : 4;
+  auto issue_lift = [&](int h) {
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (issuer && ok) {
+      fence_after_sync();
+      issue_group_k(w, tmem, NPL, opa_s, L::OPN_SPLIT, KPE, opb_s + (uint32_t)(h * (KPE / 8) * 128),
+                    NPL * KPN * 2, NPL, KPN, KPE / 16, h > 0, bar_mma);
+    }
+  };
+  auto wait_lift = [&]() {
+    const bool was_ok = ok;
+    const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
+    ok = __syncthreads_and(done) != 0;
+    if (was_ok && !ok) {
+      pending = true;
+      pending_phase = phase;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+  };
+
   for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
     const size_t e = (size_t)tile * kTile + lane;
     const float* Ft = fnb + tile * (4 * kNq * kNq * kTile);
@@ -721,6 +861,9 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
     if constexpr (WITH_NEIGH) prefetch(std::integral_constant<int, 0>{});
     static_for<0, 4>([&](auto face) {
       constexpr int s = decltype(face)::value;
+      // LIFT2: the first two faces' W are in the element operand: their pass runs while
+      // the third face's W is formed
+      if constexpr (L::LIFT2 && s == 2) issue_lift(0);
       float Wr[BT];
 #pragma unroll
       for (int m = 0; m < BT; ++m)
@@ -762,14 +905,14 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
         }
         float4* xw = reinterpret_cast<float4*>(xs) + w * kTile + lane;
 #pragma unroll
-        for (int m4 = 0; m4 < BT8 / 4; ++m4)
+        for (int m4 = 0; m4 < NM4; ++m4)
           xw[m4 * kNq * kTile] = make_float4(V[4 * m4], V[4 * m4 + 1], V[4 * m4 + 2], V[4 * m4 + 3]);
         float a[kNq];
 #pragma unroll
         for (int q = 0; q < kNq; ++q) a[q] = __ldg(Ft + ((s * kNq + w) * kNq + q) * kTile + lane);
         __syncthreads();
 #pragma unroll
-        for (int m4 = 0; m4 < BT8 / 4; ++m4) {
+        for (int m4 = 0; m4 < NM4; ++m4) {
 #pragma unroll
           for (int q = 0; q < kNq; ++q) {
             const float4 x = reinterpret_cast<const float4*>(xs)[(m4 * kNq + q) * kTile + lane];
@@ -781,31 +924,19 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
         }
         __syncthreads();
       }
-      // W^s into the element operand at K = s * BT8 + m
+      // LIFT2: the element operand is free again once the first pass has completed
+      if constexpr (L::LIFT2 && s == 2) wait_lift();
+      // W^s into the element operand at K = (s mod FH) * BT8 + m
       static_for<0, BT8 / 8>([&](auto cc) {
         constexpr int c = decltype(cc)::value;
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = (8 * c + i < BT) ? Wr[(8 * c + i < BT) ? 8 * c + i : 0] : 0.0f;
-        store_split8(opa, L::OPN_SPLIT, op_offset(my_row, s * BT8 + 8 * c, KPN), v);
+        store_split8(opa, L::OPN_SPLIT, op_offset(my_row, (s % FH) * BT8 + 8 * c, KPE), v);
       });
     });
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    if (issuer && ok) {
-      fence_after_sync();
-      issue_group(w, tmem, NPL, opa_s, L::OPN_SPLIT, KPN, opb_s, NPL, KPN, bar_mma);
-    }
-    const bool was_ok = ok;
-    const bool done = was_ok ? tc_wait(bar_mma, phase) : false;
-    ok = __syncthreads_and(done) != 0;
-    if (was_ok && !ok) {
-      pending = true;
-      pending_phase = phase;
-    }
-    phase ^= 1u;
-    fence_after_sync();
+    issue_lift(L::LIFT2 ? 1 : 0);
+    wait_lift();
     double* Qt = Q + tile * (kNq * B * kTile);
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;

@@ -722,8 +722,7 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     YT_REQUIRE(scheme->precision == YT_F64 || scheme->precision == YT_F32 ||
                    scheme->precision == YT_BF16X3_F32ACC,
                YT_ERR_UNSUPPORTED, "solver precision: YT_F64, YT_F32 or YT_BF16X3_F32ACC");
-    YT_REQUIRE(scheme->precision != YT_BF16X3_F32ACC || scheme->order <= 6, YT_ERR_UNSUPPORTED,
-               "YT_BF16X3_F32ACC solvers: orders 2..6");
+
     YT_REQUIRE(std::isfinite(scheme->dt) && scheme->dt > 0, YT_ERR_INVALID, "dt must be positive");
     YT_REQUIRE(mesh->n_elements < (int64_t(1) << 24), YT_ERR_UNSUPPORTED, "at most 2^24 elements");
     const bool nb = mesh->neighbours != nullptr;

@@ -2,7 +2,7 @@
 inputs and launch configuration (yt_step over all 31,250 tiles), checked on sampled
 elements against the oracle evaluated for each sampled element and its four neighbours
 only.  FP64 within 1e-12 (relative Frobenius norm per quantity over the sample); FP32 and
-the tensor-core form (order 6) within their stated bounds on the increment."""
+the tensor-core form within their stated bounds on the increment."""
 import functools
 
 import numpy as np
@@ -76,14 +76,15 @@ def reference(order):
     return oracle_sample(*case(order))
 
 
-# (the tensor-core form covers orders 2..6); tests of one order run consecutively so the
-# cached inputs and oracle results of that order are reused
+# tests of one order run consecutively so the cached inputs and oracle results of that
+# order are reused
 @pytest.mark.parametrize("order, prec_name, tol_q, tol_inc", [
     (6, "YT_F64", parity.F64, parity.F64_INC),
     (6, "YT_F32", None, parity.F32_INC),
     (6, "YT_BF16X3_F32ACC", None, parity.TC_INC),
     (7, "YT_F64", parity.F64, parity.F64_INC),
     (7, "YT_F32", None, parity.F32_INC),
+    (7, "YT_BF16X3_F32ACC", None, parity.TC_INC),
 ])
 def test_full_size_step_sampled(order, prec_name, tol_q, tol_inc):
     import paper_1903_11521_gb300 as yt

@@ -308,7 +308,7 @@ def test_zero_dofs_stay_zero(yt):
 
 @pytest.mark.parametrize("prec_name, order, tol, tol_el", [
     ("YT_F64", 6, 1e-12, 1e-11), ("YT_F64", 7, 1e-12, 1e-11),
-    ("YT_F32", 7, 1e-6, 3.5e-6), ("YT_BF16X3_F32ACC", 6, 4e-5, 1e-4)])
+    ("YT_F32", 7, 1e-6, 3.5e-6), ("YT_BF16X3_F32ACC", 6, 4e-5, 1e-4), ("YT_BF16X3_F32ACC", 7, 4e-5, 1e-4)])
 def test_jittered_structured_mesh_steps(yt, prec_name, order, tol, tol_el):
     """Three steps on the jittered periodic structured mesh (vertices moved by up to 0.1 h,
     the mesh family of the order-7 FP32 workload) against three oracle steps, random

@@ -47,7 +47,7 @@ def solver(yt, el, conn, Q, dt, order):
     return s
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
 def test_tc_full_step_against_fp64_oracle(yt, order):
     el, conn, Q, dt = make_case(70, order, "impedance", seed=41)
     s = solver(yt, el, conn, Q, dt, order)
@@ -62,7 +62,7 @@ def test_tc_full_step_against_fp64_oracle(yt, order):
     parity.check(f"tc step o{order} dQ", q, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
 
 
-@pytest.mark.parametrize("order", [3, 6])
+@pytest.mark.parametrize("order", [3, 6, 7])
 def test_tc_local_step(yt, order):
     """yt_step_local: k_local_tc, then the lifting kernel with the local products only."""
     el, conn, Q, dt = make_case(45, order, "unit", seed=43)
@@ -78,10 +78,11 @@ def test_tc_local_step(yt, order):
     parity.check(f"tc local o{order} dQ", q, q_ref, TC_TOL_INCREMENT, parity.TC_INC_EL, base=Q)
 
 
-def test_tc_many_tiles_and_phases(yt):
-    """More tiles than persistent CTAs (each CTA strides over several tiles), a ragged
-    last tile; yt_step equals phase 0 + phase 1 bitwise, and local + neighbour agrees."""
-    order = 4
+@pytest.mark.parametrize("order", [4, 7])
+def test_tc_many_tiles_and_phases(yt, order):
+    """More tiles than persistent CTAs (each CTA strides over several tiles: at order 7
+    every tile reloads the streamed operands), a ragged last tile; yt_step equals phase 0
+    + phase 1 bitwise, and local + neighbour agrees."""
     el, conn, Q, dt = make_case(152 * 32 * 2 + 17, order, "impedance", seed=47)
     outs = []
     for mode in ("step", "phases", "unfused"):
