@@ -407,22 +407,20 @@ def form_viscoelastic(yt, stream, n=55, order=7, steps=10, n_long=20, steps_long
     """The 27-quantity precision form: order 7, the jittered periodic structured mesh of
     n^3 x 6 tets (n = 55: 998,250), homogeneous elastic material, synthetic attenuation of
     three mechanisms per element (workload.attenuation), N(0,1) DOFs scaled by impedance
-    (stresses) and impedance x omega (anelastic functions); FP64 and FP32 contractions,
-    `steps` steps each from the same DOFs (no warm-up: both take the same steps), the FP32
-    result after them against the FP64 path (which equals the oracle to 1e-15 per step,
+    (stresses) and impedance x omega (anelastic functions); FP64, FP32 and split-bf16
+    tensor-core contractions, `steps` steps each from the same DOFs (no warm-up: all take
+    the same steps), the reduced-precision results after them against the FP64 path (which equals the oracle to 1e-15 per step,
     tests/test_gpu_viscoelastic.py).  The error after `steps_long` steps is measured the same
     way on the n_long^3 x 6 mesh of the same family (100 FP64 steps at full size take
     two minutes)."""
     out = _viscoelastic_run(yt, stream, n, order, steps)
     if steps_long:
         long = _viscoelastic_run(yt, stream, n_long, order, steps_long)
-        out["error_after_100_steps"] = {
-            "workload": long["workload"],
-            "error_vs_fp64_rel_solution": long["fp32"]["error_vs_fp64_rel_solution"],
-            "error_vs_fp64_rel_change": long["fp32"]["error_vs_fp64_rel_change"],
-            "error_vs_fp64_rel_solution_elastic": long["fp32"]["error_vs_fp64_rel_solution_elastic"],
-            "error_vs_fp64_rel_solution_anelastic": long["fp32"]["error_vs_fp64_rel_solution_anelastic"],
-            "fp64_finite": long["fp64"]["finite"]}
+        keys = ("error_vs_fp64_rel_solution", "error_vs_fp64_rel_change",
+                "error_vs_fp64_rel_solution_elastic", "error_vs_fp64_rel_solution_anelastic")
+        out["error_after_100_steps"] = {"workload": long["workload"], "fp64_finite": long["fp64"]["finite"]}
+        for key in ("fp32", "bf16x3"):
+            out["error_after_100_steps"][key] = {k: long[key][k] for k in keys}
     return out
 
 
@@ -480,15 +478,21 @@ def _viscoelastic_run(yt, stream, n, order, steps):
                    "frac_fp64_peak": (st64["local_flops"] + st64["neighbour_flops"]) * E / (t64 / 1e3) / 1e12
                    / FP64_PEAK_TFLOPS,
                    "finite": bool(np.isfinite(norm).all())}
-    q32, st32, t32, l32, n32 = run_steps(yt.YT_F32)
-    per_q = np.sqrt(sq(q32, q64))
-    out["fp32"] = {"value": E / (t32 / 1e3), "unit": METRIC, "ms_per_step": t32,
-                   "kernel_ms": {"k_local": l32, "k_neigh+k_theta": n32},
-                   "tflops": (st32["local_flops"] + st32["neighbour_flops"]) * E / (t32 / 1e3) / 1e12,
-                   "error_vs_fp64_rel_solution": float((per_q / norm).max()),
-                   "error_vs_fp64_rel_change": float((per_q / change).max()),
-                   "error_vs_fp64_rel_solution_elastic": float((per_q[:9] / norm[:9]).max()),
-                   "error_vs_fp64_rel_solution_anelastic": float((per_q[9:] / norm[9:]).max())}
+    # the reduced-precision forms one after the other, each result compared and dropped
+    # before the next runs (an order-7 27-quantity state of 1M tets is 18 GB on the host)
+    for key, prec in (("fp32", yt.YT_F32), ("bf16x3", yt.YT_BF16X3_F32ACC)):
+        qr, str_, tr, lr, nr = run_steps(prec)
+        per_q = np.sqrt(sq(qr, q64))
+        del qr
+        out[key] = {"value": E / (tr / 1e3), "unit": METRIC, "ms_per_step": tr,
+                    "kernel_ms": {"k_local": lr, "k_neigh+k_theta": nr},
+                    "tflops": (str_["local_flops"] + str_["neighbour_flops"]) * E / (tr / 1e3) / 1e12,
+                    "error_vs_fp64_rel_solution": float((per_q / norm).max()),
+                    "error_vs_fp64_rel_change": float((per_q / change).max()),
+                    "error_vs_fp64_rel_solution_elastic": float((per_q[:9] / norm[:9]).max()),
+                    "error_vs_fp64_rel_solution_anelastic": float((per_q[9:] / norm[9:]).max())}
+    out["bf16x3"]["contractions"] = ("elastic rows' global-matrix products on the tensor cores (split "
+                                     "bf16, FP32 accumulation); anelastic rows FP32 CUDA cores")
     out["flops_per_element"] = {"local": st64["local_flops"], "neighbour_and_theta": st64["neighbour_flops"]}
     out["error_definition"] = (f"after {steps} steps from the same DOFs: max over the 27 quantities "
                                "of ||Q - Q_fp64||_F / ||Q_fp64||_F (rel_solution, the same restricted to "

@@ -193,7 +193,7 @@ typedef struct yt_scheme_desc {
   int32_t flags;             /* 0, or YT_SCHEME_DIAG_EXPIRE_WAIT */
   int32_t quantities;        /* 9 (or 0): elastic; 27: viscoelastic-shaped (below) */
 } yt_scheme_desc;
-/* 27-quantity solvers (YT_F64 or YT_F32, orders 2..7).  The paper names viscoelastic
+/* 27-quantity solvers (YT_F64, YT_F32 or YT_BF16X3_F32ACC, orders 2..7).  The paper names viscoelastic
  * attenuation with three mechanisms (27 quantities, Sec. 5.1) without its equations; this
  * library reads it as the memory-variable form q = (sigma, v, theta^0, theta^1, theta^2),
  * q_t + A q_x + B q_y + C q_z = E q, with six anelastic functions theta^l per mechanism:
@@ -207,7 +207,11 @@ typedef struct yt_scheme_desc {
  * theta^l_i at 9 + 6 l + i.  yt_step, yt_step_phase (phase 1 runs two kernels: the
  * elastic neighbour flux and the anelastic rows' volume, source and fluxes) and
  * yt_step_host are available; yt_step_local / yt_step_neighbour, batches and servers are
- * elastic only (YT_ERR_UNSUPPORTED). */
+ * elastic only (YT_ERR_UNSUPPORTED).  With YT_BF16X3_F32ACC the elastic rows' products
+ * with the global matrices run on the tensor cores (split bf16), the anelastic functions'
+ * derivatives on the CUDA cores in FP32 inside the same local kernel, and the anelastic
+ * rows' volume, source and fluxes in the FP32 kernel of YT_F32; setup, the time integral
+ * and the DOF updates in binary64 as for every precision. */
 /* Diagnostics flag (no counterpart in the paper), YT_BF16X3_F32ACC solvers only: the
  * tensor-core local kernel does not issue its operand load and its first bounded wait
  * (on that load) gives up after 1 ms, before any tensor-core or bulk-copy operation is

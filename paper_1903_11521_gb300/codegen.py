@@ -220,6 +220,20 @@ int ader_upload_o{N}_{P}_{V}(const float* vals, size_t n) {{ {UPLOAD} }}
 }}  // namespace yt
 """
 
+SMALL_UNIT = """// Generated by codegen.py: the small-mesh local update (k_local_small) of polynomial
+// degree {N}, contraction type {REAL}.
+#include "ader_kernels.cuh"
+#include "yt_rows_o{N}.cuh"
+
+namespace yt {{
+void ader_set_attribute_o{N}_{P}_ls(size_t smem) {{ ader_set_attribute_small<{N}, {REAL}>(smem); }}
+void ader_launch_o{N}_{P}_ls(const AderLaunch& L) {{ ader_launch_small<{N}, {REAL}>(L); }}
+int ader_upload_o{N}_{P}_ls(const float* vals, size_t n) {{ {UPLOAD} }}
+}}  // namespace yt
+"""
+# degrees with a small-mesh local kernel (the operand column fits the registers)
+SMALL_MAX_N = 4
+
 BATCH_UNIT = """// Generated by codegen.py: the tile functions of the persistent batch kernel for
 // polynomial degree {N}, contraction type {REAL} (separately compiled, -rdc; values of the
 // sparse rows from global memory).
@@ -295,6 +309,15 @@ def generate(build_dir: str) -> list[str]:
                 upload = "(void)vals; (void)n; return 0;"
             _write_if_changed(unit, UNIT.format(N=N, P=P, V=V, LOCAL=local, FUSED=fused, UPLOAD=upload,
                                                 REAL="double" if P == "f64" else "float"))
+            units.append(unit)
+        if N <= SMALL_MAX_N:
+            unit = os.path.join(gen, f"ader_o{N}_{P}_ls.cu")
+            if P == "f32" and N <= CONST_MAX_N:
+                upload = (f"return (int)cudaMemcpyToSymbol(gen::c_vals_o{N}, vals, n * sizeof(float));")
+            else:
+                upload = "(void)vals; (void)n; return 0;"
+            _write_if_changed(unit, SMALL_UNIT.format(N=N, P=P, UPLOAD=upload,
+                                                      REAL="double" if P == "f64" else "float"))
             units.append(unit)
         unit = os.path.join(gen, f"ader_o{N}_{P}_batch_rdc.cu")
         _write_if_changed(unit, BATCH_UNIT.format(N=N, P=P, REAL="double" if P == "f64" else "float"))

@@ -279,7 +279,10 @@ __device__ __forceinline__ Real ve_row(const VeTables<Real>& V, size_t tile, int
   constexpr size_t LS = (size_t)6 * B * kTile;         // mechanism stride (theta scratch and I)
   Real* th = V.theta + ((tile * kNTheta + w) * B + K) * kTile + lane;
   double* ith = It + ((size_t)(9 + w) * B + K) * kTile + lane;
+  // the row's state and accumulators, loaded together ahead of the stores (a store to
+  // the scratch could alias the accumulators otherwise: one memory latency each)
   const Real t[3] = {th[0], th[LS], th[2 * LS]};
+  const double ti[3] = {ith[0], ith[LS], ith[2 * LS]};
   v -= (t[0] + t[1]) + t[2];                             // E_{sigma_i, theta^l_i} = -1
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
@@ -295,7 +298,7 @@ __device__ __forceinline__ Real ve_row(const VeTables<Real>& V, size_t tile, int
     u = fma(-om[l], t[l], u);                            // E_{theta, theta} = -omega_l
     u *= dtr;
     th[l * LS] = u;
-    ith[l * LS] = fma(cw, to_f64<Real, CVT>(u), ith[l * LS]);
+    ith[l * LS] = fma(cw, to_f64<Real, CVT>(u), ti[l]);
   }
   return v;
 }
@@ -402,6 +405,9 @@ __device__ __forceinline__ void ck_ve(const StepTables<Real>& T, double dt, cons
               for (int s = 0; s < 3; ++s)
                 if (s < cnt) v = fma(sc[x][s], Xsh[((x * KC + kk) * kNq + scol[s]) * kTile + lane], v);
           }
+          // stress rows of degree N: their accumulator in I, loaded before ve_row's stores
+          double* ipn = It + ((size_t)w * B + k) * kTile + lane;
+          const double in_old = (k >= NI && w < 6) ? *ipn : 0.0;
           if (w < 6) v = ve_row<N, Real, CVT, (k < NI), KC, k>(V, tile, w, lane, kk, Xsh, scol, cnt, s0, om, dtr, cw, It, v);
           v *= dtr;
           if constexpr (k < RS) D[k < RS ? k : 0] = v;
@@ -410,8 +416,7 @@ __device__ __forceinline__ void ck_ve(const StepTables<Real>& T, double dt, cons
             double* ip = Ish + (k * kNq + w) * kTile + lane;
             *ip = fma(cw, to_f64<Real, CVT>(v), *ip);
           } else if (w < 6) {
-            double* ip = It + ((size_t)w * B + k) * kTile + lane;
-            *ip = fma(cw, to_f64<Real, CVT>(v), *ip);
+            *ipn = fma(cw, to_f64<Real, CVT>(v), in_old);
           }
         }
       });
@@ -491,14 +496,33 @@ __device__ __forceinline__ void local_tile(const double* Q, double* Qout, double
       Real* th = V.theta + ((tile * kNTheta + w) * B) * kTile + lane;
       const double* qth = Qt + ((size_t)(9 + w) * B) * kTile + lane;
       double* ith = Ive + ((size_t)(9 + w) * B) * kTile + lane;
-      for (int k = 0; k < B; ++k)
+      // four rows of the three mechanisms loaded before they are stored (the stores could
+      // alias the loads otherwise: one memory latency per value)
+      static_for<0, (B + 3) / 4>([&](auto cc) {
+        constexpr int k0 = decltype(cc)::value * 4;
+        double q[3][4];
 #pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          const double q = qth[l * LS + k * kTile];
-          th[l * LS + k * kTile] = from_f64<Real, CVT>(q);
-          ith[l * LS + k * kTile] = dt * T.invfact[0] * q;
-        }
-      for (int k = NI; k < B; ++k) Ive[((size_t)w * B + k) * kTile + lane] = dt * T.invfact[0] * Qt[(w * B + k) * kTile + lane];
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) q[l][i] = (k0 + i < B) ? __ldg(qth + l * LS + (k0 + i < B ? k0 + i : 0) * kTile) : 0.0;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (k0 + i < B) {
+              th[l * LS + (k0 + i) * kTile] = from_f64<Real, CVT>(q[l][i]);
+              ith[l * LS + (k0 + i) * kTile] = dt * T.invfact[0] * q[l][i];
+            }
+      });
+      static_for<0, (B - NI + 3) / 4>([&](auto cc) {
+        constexpr int k0 = NI + decltype(cc)::value * 4;
+        double q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = (k0 + i < B) ? __ldg(Qt + (w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane) : 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (k0 + i < B) Ive[((size_t)w * B + k0 + i) * kTile + lane] = dt * T.invfact[0] * q[i];
+      });
     }
   }
 #pragma unroll
@@ -642,6 +666,163 @@ k_local(const double* Q, double* Qout, double* Iout, Real* Pface, Real* Wloc, co
   local_tile<N, LIFT, Real, VE>(Q, Qout, Iout, Pface, Wloc, star, floc, T, SP, V, tile, dt);
 }
 
+// ------------------------------------------------------------ K_local, small meshes
+// The local update with the local flux lifted (k_local<N, true, Real>) for meshes of few
+// tiles, where one CTA per 32 elements leaves most SMs idle and a tile's work on one SM
+// sets the time: one CTA per 8 elements of a tile, thread (slot q, element e) = column q
+// of element e (q = 0..8; slots 9..11 shadow quantity 8 so that every warp runs the same
+// code, and write nothing to global memory).  Same arithmetic and order of operations as
+// k_local (operand column in registers, binary64 time-integral accumulator in shared
+// memory); the lifting reads the face's flux products from registers.  Degrees whose
+// operand column fits the registers (FP64 N <= 4, FP32).
+constexpr int kSmallElems = 8;                          // elements per CTA
+constexpr int kSmallSlots = 12;                         // quantity slots
+constexpr int kSmallThreads = kSmallElems * kSmallSlots;
+template <int N, typename Real>
+constexpr size_t small_smem_bytes() {
+  using Dm = Dims<N>;
+  return (size_t)sizeof(Real) * Dm::XR * kSmallSlots * kSmallElems +
+         (size_t)8 * Dm::nd(1) * kSmallSlots * kSmallElems;
+}
+
+template <int N, typename Real>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+k_local_small(const double* Q, double* Qout, double* __restrict__ Iout, Real* __restrict__ Pface,
+              const Real* __restrict__ star, const Real* __restrict__ floc, StepTables<Real> T, StarPattern SP) {
+  using Dm = Dims<N>;
+  constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC, NI = Dm::nd(1);
+  constexpr int QS = kSmallSlots, TS = kSmallElems;
+  constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
+  static_assert(LocalRegRows<N, Real>::value == B, "the operand column must be register rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Xsh = reinterpret_cast<Real*>(smem_raw);                          // [XR][QS][TS]
+  double* Ish = reinterpret_cast<double*>(Xsh + Dm::XR * QS * TS);       // [NI][QS][TS]
+  const int q = threadIdx.x / TS, e = threadIdx.x % TS;
+  const bool act = q < kNq;
+  const int p = act ? q : kNq - 1;
+  const size_t tile = blockIdx.x / (kTile / TS);
+  const int lane = (int)(blockIdx.x % (kTile / TS)) * TS + e;           // the element's lane in its tile
+  auto xs = [&](int r, int slot) -> Real& { return Xsh[(r * QS + slot) * TS + e]; };
+  auto is = [&](int r) -> double& { return Ish[(r * QS + q) * TS + e]; };
+  const double dt = T.dt;
+  const double* Qt = Q + tile * (kNq * B * kTile);
+  double* Qo = Qout + tile * (kNq * B * kTile);
+  double* It = Iout + tile * (kNq * B * kTile);
+  const int s0 = SP.start[p], cnt = SP.start[p + 1] - s0;
+  int scol[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) scol[s] = (s < cnt) ? SP.col[s0 + s] : 0;
+  Real sc[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+      sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : Real(0);
+  auto mix = [&](int kk) {
+    Real v = Real(0);
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        if (s < cnt) v = fma(sc[x][s], xs(x * KC + kk, scol[s]), v);
+    return v;
+  };
+
+  Real D[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const double qv = __ldg(Qt + (p * B + k) * kTile + lane);
+    D[k] = from_f64<Real, CVT>(qv);
+    if (k < NI) is(k) = dt * T.invfact[0] * qv;
+  }
+  // CK derivatives in place (output row k reads rows of higher degree only)
+  const Real dtr = (Real)dt;
+  static_for<0, N>([&](auto dd) {
+    constexpr int DELTA = decltype(dd)::value;
+    constexpr int nout = Dm::nd(DELTA + 1);
+    const double cw = dt * T.invfact[DELTA + 1];
+    static_for<0, (nout + KC - 1) / KC>([&](auto chunk) {
+      constexpr int k0 = decltype(chunk)::value * KC;
+      static_for<0, KC>([&](auto kkc) {
+        constexpr int kk = decltype(kkc)::value;
+        if constexpr (k0 + kk < nout) {
+          xs(0 * KC + kk, q) = row_dotr<N, DELTA * 3 + 0, k0 + kk, Real, B>(T.val, D);
+          xs(1 * KC + kk, q) = row_dotr<N, DELTA * 3 + 1, k0 + kk, Real, B>(T.val, D);
+          xs(2 * KC + kk, q) = row_dotr<N, DELTA * 3 + 2, k0 + kk, Real, B>(T.val, D);
+        }
+      });
+      __syncthreads();
+      static_for<0, KC>([&](auto kkc) {
+        constexpr int kk = decltype(kkc)::value;
+        if constexpr (k0 + kk < nout) {
+          const Real v = mix(kk) * dtr;
+          D[k0 + kk] = v;
+          is(k0 + kk) = fma(cw, to_f64<Real, CVT>(v), is(k0 + kk));
+        }
+      });
+      __syncthreads();
+    });
+  });
+  // publish I: operand column and global memory
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const double ik = k < NI ? is(k < NI ? k : 0) : dt * T.invfact[0] * Qt[(p * B + k) * kTile + lane];
+    D[k] = from_f64<Real, CVT>(ik);
+    if (act) It[(p * B + k) * kTile + lane] = ik;
+  }
+  // volume: Q[k][p] += sum_x sum_q Astar^x_pq (Khat^x I)[k][q]
+  static_for<0, (B + KC - 1) / KC>([&](auto chunk) {
+    constexpr int k0 = decltype(chunk)::value * KC;
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      if constexpr (k0 + kk < B) {
+        xs(0 * KC + kk, q) = row_dotr<N, 18, k0 + kk, Real, B>(T.val, D);
+        xs(1 * KC + kk, q) = row_dotr<N, 19, k0 + kk, Real, B>(T.val, D);
+        xs(2 * KC + kk, q) = row_dotr<N, 20, k0 + kk, Real, B>(T.val, D);
+      }
+    });
+    __syncthreads();
+    static_for<0, KC>([&](auto kkc) {
+      constexpr int kk = decltype(kkc)::value;
+      constexpr int k = k0 + kk;
+      if constexpr (k < B) {
+        const Real v = mix(kk);
+        if (act) Qo[(p * B + k) * kTile + lane] = Qt[(p * B + k) * kTile + lane] + to_f64<Real, CVT>(v);
+      }
+    });
+    __syncthreads();
+  });
+  // local flux: Q += Rhat^s ((R^sT I) Aloc_s^T), face by face
+  Real* Pt = Pface + (tile * kTile + lane) * (4 * kNq * BT);
+  const Real* Ft = floc + tile * (4 * kNq * kNq * kTile);
+  static_for<0, 4>([&](auto face) {
+    constexpr int s = decltype(face)::value;
+    static_for<0, BT>([&](auto mm) {
+      constexpr int m = decltype(mm)::value;
+      const Real z = row_dotr<N, 21 + s, m, Real, B>(T.val, D);
+      xs(m, q) = z;
+      if (act) Pt[(s * kNq + p) * BT + m] = z;
+    });
+    Real a[kNq];
+#pragma unroll
+    for (int c = 0; c < kNq; ++c) a[c] = __ldg(Ft + ((s * kNq + p) * kNq + c) * kTile + lane);
+    __syncthreads();
+    Real Wr[BT];
+#pragma unroll
+    for (int m = 0; m < BT; ++m) {
+      Real v = Real(0);
+#pragma unroll
+      for (int c = 0; c < kNq; ++c) v = fma(a[c], xs(m, c), v);
+      Wr[m] = v;
+    }
+    __syncthreads();
+    static_for<0, B>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const Real dq = row_dotr<N, 25 + s, k, Real, BT>(T.val, Wr);
+      if (act) Qo[(p * B + k) * kTile + lane] += to_f64<Real, CVT>(dq);
+    });
+  });
+}
 // ------------------------------------------------------------- asynchronous copies
 // Global -> shared copy of one element (4 or 8 bytes) that bypasses the registers
 // (cp.async), grouped and waited for per face.
@@ -806,13 +987,14 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
 // the flux products of its two anelastic functions t = w, w + 9 (registers) and lifts
 // them into Q (one binary64 update of the column per face).
 //   Q, I   : [tile][27][B][32] double
-//   Pown   : [element][4][9][BT]  R^sT I of the elastic quantities of this launch's tiles
+//   Pown   : [element][4][9][PS]  R^sT I of the elastic quantities of this launch's tiles
+//            (rows of PS >= BT values: BT, or padded to 8 in the tensor-core form)
 //   Pface  : the same for all elements (gathered by neighbour index)
 //   fthl, fthn : [tile][4][18][9][32] anelastic rows of the local / neighbour flux solvers
 template <int N, typename Real>
 __global__ void __launch_bounds__(kNq * kTile, 1)
 k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, const Real* __restrict__ Pface,
-        const int* __restrict__ conn, const Real* __restrict__ fthl, const Real* __restrict__ fthn,
+        int PS, const int* __restrict__ conn, const Real* __restrict__ fthl, const Real* __restrict__ fthn,
         StepTables<Real> T, StarPattern SP, VeTables<Real> V) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
@@ -895,11 +1077,11 @@ k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, 
   Real* Yn = Xsh + BT * kNq * kTile;           // neighbour's, f^h applied
   static_for<0, 4>([&](auto face) {
     constexpr int sf = decltype(face)::value;
-    const Real* P = Pown + ((e * 4 + sf) * kNq + w) * BT;
+    const Real* P = Pown + ((e * 4 + sf) * kNq + w) * (size_t)PS;
     const int cn = __ldg(conn + e * 4 + sf);
     const size_t nb = (size_t)(cn >> 7);
     const int j = (cn >> 2) & 3, h = cn & 3;
-    const Real* Pn = Pface + ((nb * 4 + j) * kNq + w) * BT;
+    const Real* Pn = Pface + ((nb * 4 + j) * kNq + w) * (size_t)PS;
     Real pn[BT];
 #pragma unroll
     for (int m = 0; m < BT; ++m) {
@@ -941,10 +1123,18 @@ k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, 
         }
         Wr[m] = v;
       }
+      // Q += Rhat^s W, eight rows at a time: their loads issued together ahead of the stores
       double* qc = Qt + ((size_t)(9 + t) * B) * kTile + lane;
-      static_for<0, B>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        qc[k * kTile] += to_f64<Real, CVT>(row_dotr<N, 25 + sf, k, Real, BT>(T.val, Wr));
+      static_for<0, (B + 7) / 8>([&](auto kc) {
+        constexpr int k0 = decltype(kc)::value * 8;
+        double qv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) qv[i] = (k0 + i < B) ? qc[(k0 + i < B ? k0 + i : 0) * kTile] : 0.0;
+        static_for<0, 8>([&](auto ii) {
+          constexpr int i = decltype(ii)::value;
+          if constexpr (k0 + i < B)
+            qc[(k0 + i) * kTile] = qv[i] + to_f64<Real, CVT>(row_dotr<N, 25 + sf, k0 + i, Real, BT>(T.val, Wr));
+        });
       });
     }
     __syncthreads();
@@ -969,6 +1159,7 @@ struct AderLaunch {
   void* theta;
   const void *cth, *om, *fthl, *fthn;
   size_t smem_theta;
+  int pstride;             // values per face-projection row (0: BT)
   cudaStream_t stream;
 };
 
@@ -1033,6 +1224,20 @@ void ader_launch(const AderLaunch& L) {
   }
 }
 
+// The small-mesh local update (k_local_small): 4 CTAs of 8 elements per tile.
+template <int N, typename Real>
+void ader_set_attribute_small(size_t) {
+  cudaFuncSetAttribute(k_local_small<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)small_smem_bytes<N, Real>());
+}
+template <int N, typename Real>
+void ader_launch_small(const AderLaunch& L) {
+  k_local_small<N, Real><<<(unsigned)(L.ntiles * (kTile / kSmallElems)), kSmallThreads,
+                           small_smem_bytes<N, Real>(), L.stream>>>(
+      L.Q, L.Q, L.I, static_cast<Real*>(L.Pface), static_cast<const Real*>(L.star),
+      static_cast<const Real*>(L.floc), step_tables<Real>(L), L.SP);
+}
+
 // Kernels of a 27-quantity step: WHICH 0 = k_local (VE, fused step), 1 = k_neigh on the
 // elastic rows (fused step), 2 = k_theta.
 // Shared memory of k_theta: operand rows outside the registers (as LocalRegRows: FP64
@@ -1068,8 +1273,9 @@ void ader_launch_ve(const AderLaunch& L) {
         L.Q, L.groups, static_cast<const Real*>(L.Wloc), static_cast<const Real*>(L.fnb), L.conn, T, nullptr);
   } else {
     k_theta<N, Real><<<grid, kNq * kTile, L.smem_theta, L.stream>>>(
-        L.Q, L.I, static_cast<const Real*>(L.Pface), static_cast<const Real*>(L.groups.base[0]), L.conn,
-        static_cast<const Real*>(L.fthl), static_cast<const Real*>(L.fthn), T, L.SP, V);
+        L.Q, L.I, static_cast<const Real*>(L.Pface), static_cast<const Real*>(L.groups.base[0]),
+        L.pstride > 0 ? L.pstride : Dims<N>::BT, L.conn, static_cast<const Real*>(L.fthl),
+        static_cast<const Real*>(L.fthn), T, L.SP, V);
   }
 }
 
@@ -1100,6 +1306,19 @@ YT_DECLARE_ADER_UNIT(3, f32)
 YT_DECLARE_ADER_UNIT(4, f32)
 YT_DECLARE_ADER_UNIT(5, f32)
 YT_DECLARE_ADER_UNIT(6, f32)
+#define YT_DECLARE_ADER_SMALL(N, P)                           \
+  void ader_set_attribute_o##N##_##P##_ls(size_t);           \
+  void ader_launch_o##N##_##P##_ls(const AderLaunch&);       \
+  int ader_upload_o##N##_##P##_ls(const float*, size_t);
+YT_DECLARE_ADER_SMALL(1, f64)
+YT_DECLARE_ADER_SMALL(2, f64)
+YT_DECLARE_ADER_SMALL(3, f64)
+YT_DECLARE_ADER_SMALL(4, f64)
+YT_DECLARE_ADER_SMALL(1, f32)
+YT_DECLARE_ADER_SMALL(2, f32)
+YT_DECLARE_ADER_SMALL(3, f32)
+YT_DECLARE_ADER_SMALL(4, f32)
+#undef YT_DECLARE_ADER_SMALL
 #undef YT_DECLARE_ADER_UNIT
 #undef YT_DECLARE_ADER_VARIANT
 int ader_generated_nnz(int N);

@@ -99,7 +99,9 @@ void set_attributes() {
   cudaFuncSetAttribute(tc::k_neigh_tc<N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM_N);
 }
 
-tc::TcStep step_of(const tc::TcLaunch& L) {
+}  // namespace
+
+tc::TcStep tc_step_of(const tc::TcLaunch& L) {
   tc::TcStep T;
   T.dt = L.dt;
   T.expire_first_wait = L.expire_first_wait;
@@ -111,11 +113,16 @@ tc::TcStep step_of(const tc::TcLaunch& L) {
   return T;
 }
 
+namespace {
+
+tc::TcStep step_of(const tc::TcLaunch& L) { return tc_step_of(L); }
+
 template <int N>
 void launch_local(const tc::TcLaunch& L) {
   float* P = L.Pface + (size_t)L.tile0 * kTile * 4 * kNq * tc::Layout<N>::BT8;
   tc::k_local_tc<N><<<L.grid, tc::kRows, tc::Layout<N>::SMEM, L.stream>>>(
-      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, step_of(L), L.SP, L.ntiles, L.status);
+      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, step_of(L), L.SP, VeTables<float>{},
+      L.ntiles, L.status);
 }
 
 template <int N>

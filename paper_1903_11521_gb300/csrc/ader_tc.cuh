@@ -394,15 +394,29 @@ __device__ __forceinline__ void cp_async16(float* dst_shared, const float* src_g
 // [SROWS][9][32] (L2-resident, reused tile after tile); the time integral is summed from
 // them in binary64, in the order d = 0..N, once the derivatives are done.  Keeping the
 // binary64 accumulator in registers instead spills (168-register cap of 9-warp CTAs).
-template <int N>
+//
+// VE: 27-quantity (viscoelastic-shaped) step, Q and I [tile][27][B][32].  The source
+// couples the stress rows with the anelastic functions theta^l_i at every row, so every
+// derivative has all B rows: each one is the pass (or the two row blocks) of the first
+// derivative, K = B, for the rows of degree < N; the stress rows get the feedback
+// -sum_l theta^l_i, the rows of degree N only that.  The anelastic functions of stress
+// warp i (theta^l_i, l = 0..2) are advanced on the CUDA cores from the velocity columns
+// of the same accumulator chunks (their star rows have the stress rows' slots):
+// D~^{d+1}_theta = dt (sum_x sum_q Astar^x_theta,q X^x_q - omega_l D~^d_theta), their
+// scaled state in V.theta.  The time integral of all 27 quantities accumulates in binary64
+// in I as the derivatives are produced (I = c0 Q first).  The volume adds the source of the
+// stress rows, -sum_l I_theta; the anelastic rows' volume, source and fluxes are k_theta's.
+template <int N, bool VE = false>
 __global__ void __launch_bounds__(kRows, 1)
 k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, float* __restrict__ Wloc,
            const float* __restrict__ star, const float* __restrict__ floc,
            const unsigned char* __restrict__ blob, float* __restrict__ scratch, TcStep T, StarPattern SP,
-           int64_t ntiles, int* __restrict__ status) {
+           VeTables<float> V, int64_t ntiles, int* __restrict__ status) {
   using L = Layout<N>;
   using Dm = Dims<N>;
   constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPA = L::KPA, NI = L::NI, CS = L::CS, NV = L::NV;
+  constexpr int NQT = VE ? kNqVe : kNq;                  // quantities per element in Q and I
+  constexpr size_t LS = (size_t)6 * B * kTile;           // VE: mechanism stride of theta and I
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* opa = smem_raw;                                  // [hi | lo] 288 x KPA
   unsigned char* opb = opa + 2 * L::OPA_SPLIT;                    // global-matrix passes
@@ -540,24 +554,57 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
   };
 
   for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-    const double* Qt = Q + tile * (kNq * B * kTile);
-    double* Qo = Q + tile * (kNq * B * kTile);
+    const double* Qt = Q + tile * (NQT * B * kTile);
+    double* Qo = Q + tile * (NQT * B * kTile);
+    double* It = Iout + tile * (NQT * B * kTile);
     float sc[3][3];
 #pragma unroll
     for (int x = 0; x < 3; ++x)
 #pragma unroll
       for (int s = 0; s < 3; ++s)
         sc[x][s] = (s < cnt) ? __ldg(star + ((tile * 3 + x) * kStarSlots + s0 + s) * kTile + lane) : 0.0f;
+    // VE: relaxation rates of this stress warp's mechanisms; D~^0 of its anelastic
+    // functions into their scratch and I = c0 Q of them
+    float om[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (VE) {
+      if (w < 6) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) om[l] = __ldg(V.om + (tile * 3 + l) * kTile + lane);
+        float* th = V.theta + ((tile * kNTheta + w) * B) * kTile + lane;
+        const double* qth = Qt + ((size_t)(9 + w) * B) * kTile + lane;
+        double* ith = It + ((size_t)(9 + w) * B) * kTile + lane;
+        // four rows of the three mechanisms loaded before they are stored
+        static_for<0, (B + 3) / 4>([&](auto cc) {
+          constexpr int k0 = decltype(cc)::value * 4;
+          double q[3][4];
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[l][i] = (k0 + i < B) ? __ldg(qth + l * LS + (k0 + i < B ? k0 + i : 0) * kTile) : 0.0;
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (k0 + i < B) {
+                th[l * LS + (k0 + i) * kTile] = from_f64<float, L::INT_CVT_LOCAL>(q[l][i]);
+                ith[l * LS + (k0 + i) * kTile] = dt * T.invfact[0] * q[l][i];
+              }
+        });
+      }
+    }
 
-    // D~^0 = Q as operand (two chunks of loads in flight at a time)
+    // D~^0 = Q as operand (two chunks of loads in flight at a time); VE: I = c0 Q
     static_for<0, (up8(B) / 8 + 1) / 2>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 16;
       float v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int k = k0 + i;
-        v[i] = k < B ? from_f64<float, L::INT_CVT_LOCAL>(__ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane))
-                     : 0.0f;
+        const double q = k < B ? __ldg(Qt + (w * B + (k < B ? k : 0)) * kTile + lane) : 0.0;
+        v[i] = k < B ? from_f64<float, L::INT_CVT_LOCAL>(q) : 0.0f;
+        if constexpr (VE) {
+          if (k < B) It[(w * B + k) * kTile + lane] = dt * T.invfact[0] * q;
+        }
       }
       store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), *reinterpret_cast<float(*)[8]>(v));
       if constexpr (k0 + 8 < up8(B))
@@ -600,6 +647,153 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         else body(ub, ua);
       });
     };
+    // VE: the anelastic functions of the 8 rows kb..kb+7 of stress warp w and the source
+    // feedback into v (the stress row's star product, unscaled); HASX: the rows have
+    // accumulator chunks in xs (degree < N), else only the relaxation acts
+    // (the loads of each mechanism's rows are issued together, ahead of its stores: a
+    // store to the scratch could alias them otherwise and serialise every row on the
+    // memory latency)
+    auto ve_chunk = [&](int kb, float (&v)[8], double cw, auto hasx) {
+      constexpr bool HASX = decltype(hasx)::value;
+      float* th = V.theta + ((tile * kNTheta + w) * B + kb) * kTile + lane;
+      double* ith = It + ((size_t)(9 + w) * B + kb) * kTile + lane;
+      float t[3][8];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[l][i] = (kb + i < B) ? th[l * LS + (kb + i < B ? i : 0) * kTile] : 0.0f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] -= (t[0][i] + t[1][i]) + t[2][i];     // E_{sigma_i, theta^l_i} = -1
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        double ti[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ti[i] = (kb + i < B) ? ith[l * LS + (size_t)(kb + i < B ? i : 0) * kTile] : 0.0;
+        float u[8];
+        if constexpr (HASX) {
+          float c[3][3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              c[x][q] = (q < cnt) ? __ldg(V.cth + (((tile * 3 + l) * 3 + x) * kStressSlots + s0 + q) * kTile + lane)
+                                  : 0.0f;
+          mix_star(c, u);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) u[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          u[i] = fmaf(-om[l], t[l][i], u[i]) * dtf;                          // E_{theta, theta} = -omega_l
+          if (kb + i < B) {
+            const size_t o = l * LS + (size_t)(kb + i < B ? i : 0) * kTile;
+            th[o] = u[i];
+            ith[o] = fma(cw, to_f64<float, L::INT_CVT_LOCAL>(u[i]), ti[i]);
+          }
+        }
+      }
+    };
+    // VE: one derivative pass (row block PB of the first derivative's passes): rows
+    // ROW0 + k of D~^{d+1} from the accumulator chunks, accumulated into I, into the
+    // operand (TO_OPA) or the scratch (a first row block, while the second block's pass
+    // still reads D~^d)
+    auto mix_ve = [&](auto pb, auto to_opa, double cw) {
+      constexpr int PB = decltype(pb)::value;
+      constexpr bool TO_OPA = decltype(to_opa)::value;
+      constexpr int R = tc_rows<N>(PB), R8 = up8(R), ROW0 = tc_row0<N>(PB);
+      uint32_t ua[24], ub[24];
+      load_chunk(0, R8, ua);
+      static_for<0, R8 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value, k0 = c * 8;
+        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24]) {
+          put_chunk(cur);
+          if constexpr (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
+          // I of this chunk's rows, loaded ahead of the anelastic stores
+          double iv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = ROW0 + k0 + i;
+            iv[i] = (k < B) ? It[(w * B + (k < B ? k : 0)) * kTile + lane] : 0.0;
+          }
+          __syncthreads();
+          float v[8];
+          mix_star(sc, v);
+          if (w < 6) ve_chunk(ROW0 + k0, v, cw, std::true_type{});
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = ROW0 + k0 + i;
+            if (k < B) {
+              v[i] *= dtf;
+              It[(w * B + k) * kTile + lane] = fma(cw, to_f64<float, L::INT_CVT_LOCAL>(v[i]), iv[i]);
+              if constexpr (!TO_OPA) my_scr[(ROW0 + k0 + i) * kRows] = v[i];
+            } else {
+              v[i] = 0.0f;
+            }
+          }
+          if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
+          if constexpr (k0 + 8 < R8) __syncthreads();
+        };
+        if constexpr (c % 2 == 0) body(ua, ub);
+        else body(ub, ua);
+      });
+    };
+
+    if constexpr (VE) {
+      // the rows past the last accumulator chunk (degree N): the stress rows' feedback
+      // and the anelastic functions' relaxation only; velocity rows zero
+      constexpr int PL = L::SPLIT0 ? 1 : 0;                       // last row block
+      constexpr int KS = tc_row0<N>(PL) + up8(tc_rows<N>(PL));    // first row without a chunk
+#pragma unroll 1
+      for (int d = 0; d < N; ++d) {
+        const double cw = dt * T.invfact[d + 1];
+        const bool last = d + 1 == N;
+        if constexpr (L::SPLIT0) {
+          wait_pass(1);
+          mix_ve(std::integral_constant<int, 0>{}, std::false_type{}, cw);
+          sync_for_mma();
+          issue(1);
+          wait_pass(last ? L::ND : 0);
+          mix_ve(std::integral_constant<int, 1>{}, std::true_type{}, cw);
+          static_for<0, kSplitRows / 8>([&](auto cc) {
+            constexpr int k0 = decltype(cc)::value * 8;
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = my_scr[(k0 + i) * kRows];
+            store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+          });
+        } else {
+          wait_pass(last ? L::ND : 0);
+          mix_ve(std::integral_constant<int, 0>{}, std::true_type{}, cw);
+        }
+        static_for<0, (up8(B) - KS) / 8>([&](auto cc) {
+          constexpr int k0 = KS + decltype(cc)::value * 8;
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+          if (w < 6) {
+            double iv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) iv[i] = (k0 + i < B) ? It[(w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane] : 0.0;
+            ve_chunk(k0, v, cw, std::false_type{});
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (k0 + i < B) {
+                v[i] *= dtf;
+                It[(w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane] = fma(cw, to_f64<float, L::INT_CVT_LOCAL>(v[i]), iv[i]);
+              } else {
+                v[i] = 0.0f;
+              }
+            }
+          }
+          store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+        });
+        if (!last) {
+          sync_for_mma();
+          issue(0);
+        }
+      }
+    } else {
     static_for<0, N>([&](auto dd) {
       constexpr int DELTA = decltype(dd)::value;
       if constexpr (L::SPLIT0 && DELTA == 0) {
@@ -629,11 +823,22 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         if constexpr (P + 1 < L::ND) issue(P + 1);
       }
     });
+    }
 
     // time integral I = sum_d (dt / (d+1)!) D~^d in binary64: HBM and operand.  All loads
     // of a chunk are issued before its stores (a store to I could alias them otherwise,
-    // which serialises every row on the L2 latency).
-    double* It = Iout + tile * (kNq * B * kTile);
+    // which serialises every row on the L2 latency).  VE: I is complete; operand only.
+    if constexpr (VE) {
+      static_for<0, up8(B) / 8>([&](auto cc) {
+        constexpr int k0 = decltype(cc)::value * 8;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          v[i] = (k0 + i < B) ? from_f64<float, L::INT_CVT_LOCAL>(It[(w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane])
+                              : 0.0f;
+        store_split8(opa, L::OPA_SPLIT, op_offset(my_row, k0, KPA), v);
+      });
+    } else
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
       double qv[8];
@@ -691,7 +896,18 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int k = KB0 + k0 + i;
-            if (k0 + i < R) Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]);
+            if (k0 + i < R) {
+              if constexpr (VE) {
+                double src = 0.0;                // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
+                if (w < 6) {
+                  const double* ith = It + ((size_t)(9 + w) * B + k) * kTile + lane;
+                  src = -((ith[0] + ith[LS]) + ith[2 * LS]);
+                }
+                Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]) + src;
+              } else {
+                Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]);
+              }
+            }
           }
           if constexpr (k0 + 8 < R8) __syncthreads();
         };
@@ -774,7 +990,8 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 // tensor-core pass with K = the four faces' W stacked (s * BT8 + m).
 //   WITH_LOCAL: add the local flux products written by k_local_tc
 //   WITH_NEIGH: add the neighbour contributions (gathered face projections)
-template <int N, bool WITH_LOCAL, bool WITH_NEIGH>
+//   NQT: quantities per element of Q (27: the elastic rows of a 27-quantity step)
+template <int N, bool WITH_LOCAL, bool WITH_NEIGH, int NQT = kNq>
 __global__ void __launch_bounds__(kRows, 1)
 k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__ Wloc,
            const float* __restrict__ fnb, const int* __restrict__ conn, const float* __restrict__ fmat,
@@ -937,7 +1154,7 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
     });
     issue_lift(L::LIFT2 ? 1 : 0);
     wait_lift();
-    double* Qt = Q + tile * (kNq * B * kTile);
+    double* Qt = Q + tile * (NQT * B * kTile);
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
       float r[8];
@@ -970,6 +1187,7 @@ struct TcLaunch {
   const int* conn;
   const unsigned char *blob_local, *blob_neigh;
   float* scratch;            // grid x Layout<N>::SROWS x 288 floats
+  VeTables<float> ve;        // 27-quantity steps: anelastic scratch, star rows, rates
   double dt;
   StarPattern SP;
   int* status;
@@ -990,5 +1208,11 @@ void tc_set_attributes(int N);
 void tc_launch_local(int N, const tc::TcLaunch& L);
 // variant 0: local + neighbour products (fused step), 1: neighbour only, 2: local only
 void tc_launch_neigh(int N, const tc::TcLaunch& L, int variant);
+// 27-quantity step (ader_tc_ve.cu): k_local_tc<N, true>, then the fused lifting of the
+// elastic rows
+tc::TcStep tc_step_of(const tc::TcLaunch& L);       // dt and 1/(d+1)! of a launch
+void tc_set_attributes_ve(int N);
+void tc_launch_local_ve(int N, const tc::TcLaunch& L);
+void tc_launch_neigh_ve(int N, const tc::TcLaunch& L);
 
 }  // namespace yt

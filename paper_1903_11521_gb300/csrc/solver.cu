@@ -364,6 +364,7 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
   L.fthl = s->fthl_r;
   L.fthn = s->fthn_r;
   L.smem_theta = s->smem_theta;
+  L.pstride = s->prec == YT_BF16X3_F32ACC ? tc::up8(s->BT) : s->BT;
   L.stream = st;
   return L;
 }
@@ -387,6 +388,37 @@ AderLaunch launch_args(yt_solver* s, cudaStream_t st) {
     }                                                                          \
   } while (0)
 
+// The small-mesh local kernel of degree N <= 4 and the solver's contraction type
+#define YT_SMALL_SWITCH(FN, ...)                                               \
+  do {                                                                         \
+    switch (s->N * 2 + (s->prec == YT_F32 ? 1 : 0)) {                          \
+      case 2: FN##_o1_f64_ls(__VA_ARGS__); break;                             \
+      case 3: FN##_o1_f32_ls(__VA_ARGS__); break;                             \
+      case 4: FN##_o2_f64_ls(__VA_ARGS__); break;                             \
+      case 5: FN##_o2_f32_ls(__VA_ARGS__); break;                             \
+      case 6: FN##_o3_f64_ls(__VA_ARGS__); break;                             \
+      case 7: FN##_o3_f32_ls(__VA_ARGS__); break;                             \
+      case 8: FN##_o4_f64_ls(__VA_ARGS__); break;                             \
+      case 9: FN##_o4_f32_ls(__VA_ARGS__); break;                             \
+      default: throw Error(YT_ERR_UNSUPPORTED, "no small-mesh kernel for this order"); \
+    }                                                                          \
+  } while (0)
+
+// k_theta of the FP32 contraction type whatever the solver's precision (the anelastic
+// rows of a tensor-core 27-quantity step run on the CUDA cores in FP32)
+#define YT_THETA_F32_SWITCH(FN, ...)                                           \
+  do {                                                                         \
+    switch (s->N) {                                                            \
+      case 1: FN##_o1_f32_vt(__VA_ARGS__); break;                             \
+      case 2: FN##_o2_f32_vt(__VA_ARGS__); break;                             \
+      case 3: FN##_o3_f32_vt(__VA_ARGS__); break;                             \
+      case 4: FN##_o4_f32_vt(__VA_ARGS__); break;                             \
+      case 5: FN##_o5_f32_vt(__VA_ARGS__); break;                             \
+      case 6: FN##_o6_f32_vt(__VA_ARGS__); break;                             \
+      default: throw Error(YT_ERR_UNSUPPORTED, "no kernel for this order");    \
+    }                                                                          \
+  } while (0)
+
 // Shared memory of the two kernels of degree N: k_local holds the operand rows not kept
 // in registers, the exchange buffer and (with register operands) the time-integral
 // accumulator; k_neigh the four faces' flux products.
@@ -401,6 +433,12 @@ void set_smem(yt_solver* s) {
     YT_REQUIRE(s->smem_local <= (size_t)optin && s->smem_neigh <= (size_t)optin, YT_ERR_UNSUPPORTED,
                "tensor-core step: shared memory of this order exceeds the device limit");
     tc_set_attributes(N);
+    if (s->P == kNqVe) {
+      tc_set_attributes_ve(N);
+      s->smem_theta = ader_theta_smem(N, true);
+      YT_REQUIRE(s->smem_theta <= (size_t)optin, YT_ERR_UNSUPPORTED, "order too high for this precision");
+      YT_THETA_F32_SWITCH(ader_set_attribute, s->smem_theta);
+    }
     cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
     return;
   }
@@ -421,6 +459,12 @@ void set_smem(yt_solver* s) {
   YT_VARIANT_SWITCH(ader_set_attribute, ll, s->smem_local);
   YT_VARIANT_SWITCH(ader_set_attribute, nf, s->smem_neigh);
   YT_VARIANT_SWITCH(ader_set_attribute, np, s->smem_neigh);
+  // small meshes: the local update on 8-element CTAs when the tiles do not fill the SMs
+  int dev = 0, sms = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  s->small_local = N <= 4 && s->ntiles <= sms;
+  if (s->small_local) YT_SMALL_SWITCH(ader_set_attribute, 0);
   cuda_check(cudaGetLastError(), "cudaFuncSetAttribute");
 }
 
@@ -431,8 +475,8 @@ tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt =
   L.ntiles = nt;
   L.tile0 = t0;
   L.grid = (unsigned)std::min<int64_t>(nt, s->tc_grid);
-  L.Q = s->Q + e0 * kNq * s->B;
-  L.I = s->I + e0 * kNq * s->B;
+  L.Q = s->Q + e0 * s->P * s->B;
+  L.I = s->I + e0 * s->P * s->B;
   L.Pface = static_cast<float*>(s->Pface);             // gathered by absolute index
   L.Wloc = static_cast<float*>(s->Wloc) + e0 * 4 * kNq * s->BT;
   L.star = static_cast<const float*>(s->star_r) + e0 * 3 * kStarSlots;
@@ -443,6 +487,12 @@ tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt =
   L.blob_local = s->d_tc_local;
   L.scratch = s->d_tc_scratch;
   L.blob_neigh = s->d_tc_neigh;
+  L.ve = VeTables<float>{};
+  if (s->P == kNqVe) {
+    L.ve.theta = static_cast<float*>(s->theta) + e0 * kNTheta * s->B;
+    L.ve.cth = static_cast<const float*>(s->cth_r) + e0 * 3 * 3 * kStressSlots;
+    L.ve.om = static_cast<const float*>(s->om_r) + e0 * 3;
+  }
   L.dt = s->dt;
   L.SP = kStar;
   L.status = s->d_status;
@@ -466,7 +516,7 @@ AderLaunch chunk_args(const AderLaunch& F, const yt_solver* s, int64_t t0, int64
     L.fthl = static_cast<const unsigned char*>(L.fthl) + (size_t)t0 * 4 * kNTheta * kNq * kTile * rb;
     L.fthn = static_cast<const unsigned char*>(L.fthn) + (size_t)t0 * 4 * kNTheta * kNq * kTile * rb;
   }
-  L.Pface = static_cast<unsigned char*>(L.Pface) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
+  L.Pface = static_cast<unsigned char*>(L.Pface) + (size_t)t0 * kTile * 4 * kNq * L.pstride * rb;
   L.Wloc = static_cast<unsigned char*>(L.Wloc) + (size_t)t0 * kTile * 4 * kNq * s->BT * rb;
   L.star = static_cast<const unsigned char*>(L.star) + (size_t)t0 * 3 * kStarSlots * kTile * rb;
   L.floc = static_cast<const unsigned char*>(L.floc) + (size_t)t0 * 4 * 81 * kTile * rb;
@@ -475,13 +525,38 @@ AderLaunch chunk_args(const AderLaunch& F, const yt_solver* s, int64_t t0, int64
   return L;
 }
 
+// Tensor-core form, fused step over tiles [t0, t0 + nt): phase 0 k_local_tc, phase 1 the
+// lifting kernel (local and neighbour products through Rhat^s); 27 quantities: the
+// elastic rows so, and k_theta (FP32 CUDA cores) for the anelastic rows after them.
+void dispatch_tc_fused(yt_solver* s, cudaStream_t st, int phase, int64_t t0, int64_t nt) {
+  const tc::TcLaunch T = tc_args(s, st, t0, nt);
+  if (s->P == kNqVe) {
+    if (phase == 0) {
+      tc_launch_local_ve(s->N, T);
+    } else {
+      tc_launch_neigh_ve(s->N, T);
+      const AderLaunch L = chunk_args(launch_args(s, st), s, t0, T.ntiles);
+      YT_THETA_F32_SWITCH(ader_launch, L);
+    }
+  } else if (phase == 0) {
+    tc_launch_local(s->N, T);
+  } else {
+    tc_launch_neigh(s->N, T, 0);
+  }
+}
+
 // Tensor-core form: k_local_tc writes the local flux products, and the lifting kernel
 // adds them (fused step: with the neighbour products) through Rhat^s.
 void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
   if (s->prec == YT_BF16X3_F32ACC) {
-    const tc::TcLaunch T = tc_args(s, st);
-    tc_launch_local(s->N, T);
-    if (!fused) tc_launch_neigh(s->N, T, 2);
+    if (fused) {
+      dispatch_tc_fused(s, st, 0, 0, -1);
+    } else {
+      YT_REQUIRE(s->P == kNq, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
+      const tc::TcLaunch T = tc_args(s, st);
+      tc_launch_local(s->N, T);
+      tc_launch_neigh(s->N, T, 2);
+    }
     cuda_check(cudaGetLastError(), "k_local_tc launch");
     return;
   }
@@ -491,6 +566,8 @@ void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
     YT_VARIANT_SWITCH(ader_launch, vl, L);
   } else if (fused) {
     YT_VARIANT_SWITCH(ader_launch, lf, L);
+  } else if (s->small_local) {
+    YT_SMALL_SWITCH(ader_launch, L);
   } else {
     YT_VARIANT_SWITCH(ader_launch, ll, L);
   }
@@ -498,7 +575,12 @@ void dispatch_local(yt_solver* s, cudaStream_t st, bool fused) {
 }
 void dispatch_neigh(yt_solver* s, cudaStream_t st, bool fused) {
   if (s->prec == YT_BF16X3_F32ACC) {
-    tc_launch_neigh(s->N, tc_args(s, st), fused ? 0 : 1);
+    if (fused) {
+      dispatch_tc_fused(s, st, 1, 0, -1);
+    } else {
+      YT_REQUIRE(s->P == kNq, YT_ERR_UNSUPPORTED, "27-quantity solvers: fused step only (yt_step, yt_step_phase)");
+      tc_launch_neigh(s->N, tc_args(s, st), 1);
+    }
     cuda_check(cudaGetLastError(), "k_neigh_tc launch");
     return;
   }
@@ -639,6 +721,17 @@ void build_tables(yt_solver* s) {
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
     s->tc_grid = (unsigned)std::min<int64_t>(s->ntiles, sms);
     s->d_tc_scratch = dalloc<float>(tc_scratch_floats(N, s->tc_grid));
+    if (s->P == kNqVe) {
+      // k_theta (FP32): its sparse lists' values, from constant memory too at degree <= 5
+      std::vector<float> v32(csr.val.begin(), csr.val.end());
+      if (N <= 5) {
+        int rc = 0;
+        YT_THETA_F32_SWITCH(rc |= ader_upload, v32.data(), v32.size());
+        YT_REQUIRE(rc == 0, YT_ERR_CUDA, "upload of constant values failed");
+      }
+      s->d_val32 = dalloc<float>(v32.size());
+      cuda_check(cudaMemcpy(s->d_val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy val32");
+    }
   }
   if (s->prec == YT_F32) {
     std::vector<float> v32(csr.val.begin(), csr.val.end()), f32(R.f.begin(), R.f.end());
@@ -653,6 +746,7 @@ void build_tables(yt_solver* s) {
       } else {
         YT_VARIANT_SWITCH(rc |= ader_upload, lf, v32.data(), v32.size());
         YT_VARIANT_SWITCH(rc |= ader_upload, ll, v32.data(), v32.size());
+        if (N <= 4) YT_SMALL_SWITCH(rc |= ader_upload, v32.data(), v32.size());
         YT_VARIANT_SWITCH(rc |= ader_upload, nf, v32.data(), v32.size());
         YT_VARIANT_SWITCH(rc |= ader_upload, np, v32.data(), v32.size());
       }
@@ -732,8 +826,9 @@ extern "C" yt_status yt_solver_create(const yt_mesh_desc* mesh, const yt_scheme_
     const bool ve = scheme->quantities == kNqVe;
     YT_REQUIRE(!ve || mesh->attenuation, YT_ERR_INVALID, "27-quantity solvers need the attenuation parameters");
     YT_REQUIRE(ve || !mesh->attenuation, YT_ERR_INVALID, "attenuation parameters given to a 9-quantity solver");
-    YT_REQUIRE(!ve || scheme->precision == YT_F64 || scheme->precision == YT_F32, YT_ERR_UNSUPPORTED,
-               "27-quantity solvers: YT_F64 or YT_F32");
+    YT_REQUIRE(!ve || scheme->precision == YT_F64 || scheme->precision == YT_F32 ||
+                   scheme->precision == YT_BF16X3_F32ACC,
+               YT_ERR_UNSUPPORTED, "27-quantity solvers: YT_F64, YT_F32 or YT_BF16X3_F32ACC");
     YT_REQUIRE(!ve || nb, YT_ERR_INVALID, "27-quantity solvers need the face connectivity");
     YT_REQUIRE(mesh->n_halo >= 0 && mesh->n_halo < (int64_t(1) << 26), YT_ERR_INVALID, "n_halo out of range");
     YT_REQUIRE(mesh->n_halo == 0 || (nb && !ve && scheme->precision != YT_BF16X3_F32ACC), YT_ERR_UNSUPPORTED,
@@ -947,9 +1042,7 @@ namespace {
 // phase 1: k_neigh of the fused step).
 void dispatch_chunk(yt_solver* s, cudaStream_t st, int phase, int64_t t0, int64_t nt) {
   if (s->prec == YT_BF16X3_F32ACC) {
-    const tc::TcLaunch T = tc_args(s, st, t0, nt);
-    if (phase == 0) tc_launch_local(s->N, T);
-    else tc_launch_neigh(s->N, T, 0);
+    dispatch_tc_fused(s, st, phase, t0, nt);
   } else {
     const AderLaunch L = chunk_args(launch_args(s, st), s, t0, nt);
     if (s->P == kNqVe) {

@@ -35,6 +35,7 @@ struct yt_solver {
   float* d_tc_scratch = nullptr;
   int* d_status = nullptr;
   unsigned tc_grid = 0;
+  bool small_local = false;   // yt_step_local on the small-mesh kernel (tiles <= SMs)
   bool diag_expire_wait = false;     // YT_SCHEME_DIAG_EXPIRE_WAIT
   // 27 quantities: anelastic star slots, relaxation frequencies and flux-solver rows (FP64
   // setup copies and the contraction type's), the derivative scratch of the anelastic

@@ -96,3 +96,7 @@ TC_I, TC_I_EL = 4e-5, 6e-5
 # roundings per step.  Bounds about nine times these.
 VE_F32_INC, VE_F32_INC_EL = 2.5e-6, 5e-7
 VE_F32_I, VE_F32_I_EL = 2e-7, 3e-7
+# 27 quantities, split-bf16 tensor cores for the elastic rows (the anelastic functions in
+# FP32 from the same accumulators): the elastic bounds, to be narrowed once measured.
+VE_TC_INC, VE_TC_INC_EL = TC_INC, TC_INC_EL
+VE_TC_I, VE_TC_I_EL = TC_I, TC_I_EL

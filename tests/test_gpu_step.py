@@ -92,6 +92,42 @@ def test_config1_local_update_unit_dofs(yt):
     parity.check("f64 config1 Q", q_gpu, q_ref, TOL, TOL)
 
 
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+@pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32"])
+def test_small_mesh_local_kernel_equals_tile_kernel(yt, order, prec_name):
+    """The local update of a mesh of at most one tile per SM runs on 8-element CTAs
+    (k_local_small, orders <= 5); one tile more selects the 32-element kernel.  The local
+    update is element-local, so the first elements of the larger mesh must come out
+    bitwise as in the smaller mesh (same arithmetic in the same order), with a ragged
+    last tile; both against the oracle."""
+    import torch
+    prec = getattr(yt, prec_name)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    E_small = 32 * sms - 5                       # ragged last tile, tiles = SMs
+    E_big = 32 * sms + 40                        # tiles > SMs
+    el, conn, Q, dt = make_case(E_big, order, "impedance", seed=33)
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    outs = []
+    for E in (E_small, E_big):
+        s = yt.Solver(order, dt, mat[:E], el.jac[:E], None, None, None, precision=prec)
+        s.set_dofs_host(Q[:E])
+        s.step_local()
+        outs.append((s.get_host()[:E_small], s.get_host(yt.YT_FIELD_TIME_INTEGRAL)[:E_small]))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    sub = np.arange(0, E_small, 97)
+    star, loc, nb = scheme.setup_element_matrices(el.rho[sub], el.lam[sub], el.mu[sub], el.jac[sub])
+    _, I = scheme.derivatives_and_time_integral(Q[sub], star, dt, order - 1)
+    q_ref = scheme.local_update(Q[sub], I, star, loc, order - 1)
+    if prec == yt.YT_F64:
+        parity.check(f"small-mesh local o{order} f64 I", outs[0][1][sub], I, TOL, TOL)
+        parity.check(f"small-mesh local o{order} f64 dQ", outs[0][0][sub], q_ref, parity.F64_INC,
+                     parity.F64_INC, base=Q[sub])
+    else:
+        parity.check(f"small-mesh local o{order} f32 dQ", outs[0][0][sub], q_ref, parity.F32_INC,
+                     parity.F32_INC_EL, base=Q[sub])
+
+
 def test_plane_wave_on_device(yt):
     """Several steps on the periodic mesh: matches the oracle step by step and converges
     to the closed-form plane wave like the oracle does."""

@@ -1,8 +1,8 @@
 """27-quantity (viscoelastic-shaped) step on the device against the oracle of
 oracle/viscoelastic.py: FP64 within 1e-12 (per quantity and per element, the nine
-elastic quantities and the eighteen anelastic functions alike), FP32 within the bounds of
-tests/parity.py; yt_step = phase 0 + phase 1 and = yt_step_host bitwise; several steps
-on the jittered structured mesh; degenerate inputs."""
+elastic quantities and the eighteen anelastic functions alike), FP32 and the split-bf16
+tensor-core form within the bounds of tests/parity.py; yt_step = phase 0 + phase 1 and =
+yt_step_host bitwise; several steps on the jittered structured mesh; degenerate inputs."""
 import numpy as np
 import pytest
 
@@ -75,7 +75,25 @@ def test_ve_fp32_step_against_oracle(yt, order):
     parity.check(f"ve f32 o{order} dQ", q, q_ref, parity.VE_F32_INC, parity.VE_F32_INC_EL, base=Q)
 
 
-@pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32"])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+def test_ve_bf16x3_step_against_oracle(yt, order):
+    """Tensor-core form: the elastic rows' global-matrix products in split bf16 (every
+    derivative on the first derivative's passes, all B rows), the anelastic functions on
+    the CUDA cores in FP32, binary64 time integral and updates."""
+    E = 70 if order < 7 else 45
+    el, conn, dt, att, Q = make_case(E, order, 580 + order)
+    s = solver(yt, el, conn, dt, att, order, yt.YT_BF16X3_F32ACC)
+    s.set_dofs_host(Q)
+    s.step()
+    q, i = s.get_host(), s.get_host(yt.YT_FIELD_TIME_INTEGRAL)
+    s.status()
+    s.close()
+    q_ref, I_ref = oracle_steps(el, conn, dt, att, Q, order)
+    parity.check(f"ve bf16x3 o{order} I", i, I_ref, parity.VE_TC_I, parity.VE_TC_I_EL)
+    parity.check(f"ve bf16x3 o{order} dQ", q, q_ref, parity.VE_TC_INC, parity.VE_TC_INC_EL, base=Q)
+
+
+@pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32", "YT_BF16X3_F32ACC"])
 def test_ve_phases_and_host_step_equal_step(yt, prec_name):
     """yt_step == phase 0 + phase 1 and == yt_step_host (8 element chunks, ragged last
     chunk and tile) bitwise."""
@@ -107,7 +125,7 @@ def test_ve_phases_and_host_step_equal_step(yt, prec_name):
 
 
 @pytest.mark.parametrize("prec_name, order, tol, tol_el", [
-    ("YT_F64", 7, 1e-12, 1e-11), ("YT_F32", 7, None, None)])
+    ("YT_F64", 7, 1e-12, 1e-11), ("YT_F32", 7, None, None), ("YT_BF16X3_F32ACC", 7, "tc", None)])
 def test_ve_jittered_mesh_three_steps(yt, prec_name, order, tol, tol_el):
     """Three steps on the jittered periodic structured mesh (the mesh family of the
     order-7, 27-quantity workload) against three oracle steps; errors of each quantity
@@ -127,24 +145,24 @@ def test_ve_jittered_mesh_three_steps(yt, prec_name, order, tol, tol_el):
     Q, _ = oracle_steps(el, mesh.conn, dt, att, Q0, order, steps=3)
     if tol is None:
         tol, tol_el = parity.VE_F32_INC, parity.VE_F32_INC_EL
+    elif tol == "tc":
+        tol, tol_el = parity.VE_TC_INC, parity.VE_TC_INC_EL
     parity.check(f"ve {prec_name} jittered o{order} 3 steps dQ", q, Q, tol, tol_el, base=Q0)
 
 
 def test_ve_degenerate_inputs(yt):
-    """Zero DOFs stay exactly zero; a single element whose faces are its own neighbours;
-    the unfused pair and the tensor-core form are refused for 27 quantities."""
+    """Zero DOFs stay exactly zero (FP32 and tensor-core forms); a single element whose
+    faces are its own neighbours; the unfused pair is refused for 27 quantities."""
     el, conn, dt, att, Q = make_case(40, 4, 560)
-    s = solver(yt, el, conn, dt, att, 4, yt.YT_F32)
-    s.set_dofs_host(np.zeros_like(Q))
-    s.step()
-    assert not np.any(s.get_host()) and not np.any(s.get_host(yt.YT_FIELD_TIME_INTEGRAL))
-    with pytest.raises(yt.YtError) as info:
-        s.step_local()
-    assert info.value.status == 4
-    s.close()
-    with pytest.raises(yt.YtError) as info:
-        solver(yt, el, conn, dt, att, 4, yt.YT_BF16X3_F32ACC)
-    assert info.value.status == 4
+    for prec in (yt.YT_F32, yt.YT_BF16X3_F32ACC):
+        s = solver(yt, el, conn, dt, att, 4, prec)
+        s.set_dofs_host(np.zeros_like(Q))
+        s.step()
+        assert not np.any(s.get_host()) and not np.any(s.get_host(yt.YT_FIELD_TIME_INTEGRAL))
+        with pytest.raises(yt.YtError) as info:
+            s.step_local()
+        assert info.value.status == 4
+        s.close()
     # one element, faces paired 0-3 and 1-2 with itself
     e1 = wl.random_elements(1, seed=561)
     dt1 = wl.cfl_time_step(e1, 4)
