@@ -97,6 +97,9 @@ TC_I, TC_I_EL = 4e-5, 6e-5
 VE_F32_INC, VE_F32_INC_EL = 2.5e-6, 5e-7
 VE_F32_I, VE_F32_I_EL = 2e-7, 3e-7
 # 27 quantities, split-bf16 tensor cores for the elastic rows (the anelastic functions in
-# FP32 from the same accumulators): the elastic bounds, to be narrowed once measured.
-VE_TC_INC, VE_TC_INC_EL = TC_INC, TC_INC_EL
-VE_TC_I, VE_TC_I_EL = TC_I, TC_I_EL
+# FP32 from the same accumulators): measured 8.6e-6 per quantity and 3.5e-7 per element on
+# the increment (orders 2..7, random mesh and 3 steps on the jittered mesh), 3.6e-7 / 3.1e-8
+# on the time integral; as in FP32 the anelastic functions carry most of an element's norm
+# and see only FP32 roundings.  Bounds about nine times these.
+VE_TC_INC, VE_TC_INC_EL = 8e-5, 3.5e-6
+VE_TC_I, VE_TC_I_EL = 3.5e-6, 3e-7
