@@ -974,6 +974,11 @@ k_neigh(double* Q, FaceGroups G, const Real* Wloc, const Real* fnb, const int* c
 }
 
 // ------------------------------------------------------------------------- K_theta
+// faces whose staged projections k_theta holds at once
+template <typename Real>
+struct ThetaFacesPerPass {
+  static constexpr int value = sizeof(Real) == 4 ? 2 : 1;
+};
 // The anelastic rows of a 27-quantity step (after k_local<N, false, Real, true>, beside
 // k_neigh<N, true, Real, 27>, which updates only the elastic rows): for each anelastic
 // function t = (l, i) of mechanism l and component i,
@@ -998,13 +1003,16 @@ k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, 
         StepTables<Real> T, StarPattern SP, VeTables<Real> V) {
   using Dm = Dims<N>;
   constexpr int B = Dm::B, BT = Dm::BT, KC = Dm::KC;
-  constexpr int RS = LocalRegRows<N, Real>::value;
-  constexpr int SD = RS > 0 ? RS : 1;
+  // the volume's operand column in shared memory: in registers it left too few for the
+  // face phase, which then spilled (kilobytes of local memory per thread)
+  constexpr int RS = 0;
+  constexpr int SD = 1;
   constexpr bool CVT = MinBlocks<N, Real, true>::int_cvt;
   constexpr size_t TQ = (size_t)kNqVe * B * kTile;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* Dsh = reinterpret_cast<Real*>(smem_raw);            // operand rows >= RS: [B - RS][9][32]
-  Real* Xsh = Dsh + (B - RS) * kNq * kTile;                 // [KC][9][32] volume, then [2][BT][9][32]
+  Real* Dsh = reinterpret_cast<Real*>(smem_raw);            // volume operand rows [B][9][32]
+  Real* Xsh = Dsh + B * kNq * kTile;                        // volume exchange [KC][9][32]
+  Real* Xf = Dsh;                                           // then the faces [2 FP][BT][9][32]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t tile = blockIdx.x;
   const size_t e = tile * kTile + lane;
@@ -1072,58 +1080,74 @@ k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, 
     __syncthreads();
   });
 
-  // ---- fluxes, face by face
-  Real* Yl = Xsh;                              // own projections   [BT][9][32]
-  Real* Yn = Xsh + BT * kNq * kTile;           // neighbour's, f^h applied
-  static_for<0, 4>([&](auto face) {
-    constexpr int sf = decltype(face)::value;
-    const Real* P = Pown + ((e * 4 + sf) * kNq + w) * (size_t)PS;
-    const int cn = __ldg(conn + e * 4 + sf);
-    const size_t nb = (size_t)(cn >> 7);
-    const int j = (cn >> 2) & 3, h = cn & 3;
-    const Real* Pn = Pface + ((nb * 4 + j) * kNq + w) * (size_t)PS;
-    Real pn[BT];
-#pragma unroll
-    for (int m = 0; m < BT; ++m) {
-      Yl[(m * kNq + w) * kTile + lane] = P[m];
-      pn[m] = Pn[m];
-    }
-    const Real* fh = T.f + (size_t)h * BT * BT;
-#pragma unroll
-    for (int d = 0; d <= N; ++d) {
-      const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
-#pragma unroll
-      for (int m = lo; m < hi; ++m) {
-        Real v = Real(0);
-#pragma unroll
-        for (int n = lo; n < hi; ++n) v = fma(__ldg(fh + m + n * BT), pn[n], v);
-        Yn[(m * kNq + w) * kTile + lane] = v;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int t = w + 9 * c;
-      const Real* al = fthl + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
-      const Real* an = fthn + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
-      Real a[kNq], b[kNq];
-#pragma unroll
-      for (int q = 0; q < kNq; ++q) {
-        a[q] = __ldg(al + q * kTile);
-        b[q] = __ldg(an + q * kTile);
-      }
-      Real Wr[BT];
+  // ---- fluxes, FP faces per pass (FP32: two, so that the anelastic rows of Q are
+  // read-modify-written twice instead of four times; FP64: one, two faces' staged
+  // projections do not fit beside the shared operand rows)
+  constexpr int FP = ThetaFacesPerPass<Real>::value;
+  static_for<0, 4 / FP>([&](auto pass) {
+    constexpr int f0 = decltype(pass)::value * FP;
+    // own projections Yl [BT][9][32] and the neighbour's with f^h applied Yn, per face
+    static_for<0, FP>([&](auto ff) {
+      constexpr int sf = f0 + decltype(ff)::value;
+      Real* Yl = Xf + (2 * decltype(ff)::value) * BT * kNq * kTile;
+      Real* Yn = Yl + BT * kNq * kTile;
+      const Real* P = Pown + ((e * 4 + sf) * kNq + w) * (size_t)PS;
+      const int cn = __ldg(conn + e * 4 + sf);
+      const size_t nb = (size_t)(cn >> 7);
+      const int j = (cn >> 2) & 3, h = cn & 3;
+      const Real* Pn = Pface + ((nb * 4 + j) * kNq + w) * (size_t)PS;
+      Real pn[BT];
 #pragma unroll
       for (int m = 0; m < BT; ++m) {
-        Real v = Real(0);
+        Yl[(m * kNq + w) * kTile + lane] = P[m];
+        pn[m] = Pn[m];
+      }
+      const Real* fh = T.f + (size_t)h * BT * BT;
+#pragma unroll
+      for (int d = 0; d <= N; ++d) {
+        const int lo = d * (d + 1) / 2, hi = (d + 1) * (d + 2) / 2;
+#pragma unroll
+        for (int m = lo; m < hi; ++m) {
+          Real v = Real(0);
+#pragma unroll
+          for (int n = lo; n < hi; ++n) v = fma(__ldg(fh + m + n * BT), pn[n], v);
+          Yn[(m * kNq + w) * kTile + lane] = v;
+        }
+      }
+    });
+    __syncthreads();
+    // one column after the other (unrolled, the two columns' lifting sequences were
+    // interleaved and spilled kilobytes per thread)
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int t = w + 9 * c;
+      // W^s = (R^sT I) Aloc_s,t^T + (f^h R^jT I_nb) Anb_s,t^T of the pass's faces
+      Real Wr[FP][BT];
+      static_for<0, FP>([&](auto ff) {
+        constexpr int fi = decltype(ff)::value, sf = f0 + fi;
+        const Real* Yl = Xf + (2 * fi) * BT * kNq * kTile;
+        const Real* Yn = Yl + BT * kNq * kTile;
+        const Real* al = fthl + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
+        const Real* an = fthn + (((tile * 4 + sf) * kNTheta + t) * kNq) * kTile + lane;
+        Real a[kNq], b[kNq];
 #pragma unroll
         for (int q = 0; q < kNq; ++q) {
-          v = fma(a[q], Yl[(m * kNq + q) * kTile + lane], v);
-          v = fma(b[q], Yn[(m * kNq + q) * kTile + lane], v);
+          a[q] = __ldg(al + q * kTile);
+          b[q] = __ldg(an + q * kTile);
         }
-        Wr[m] = v;
-      }
-      // Q += Rhat^s W, eight rows at a time: their loads issued together ahead of the stores
+#pragma unroll
+        for (int m = 0; m < BT; ++m) {
+          Real v = Real(0);
+#pragma unroll
+          for (int q = 0; q < kNq; ++q) {
+            v = fma(a[q], Yl[(m * kNq + q) * kTile + lane], v);
+            v = fma(b[q], Yn[(m * kNq + q) * kTile + lane], v);
+          }
+          Wr[fi][m] = v;
+        }
+      });
+      // Q += sum_s Rhat^s W^s, eight rows at a time: their loads issued together ahead of
+      // the stores
       double* qc = Qt + ((size_t)(9 + t) * B) * kTile + lane;
       static_for<0, (B + 7) / 8>([&](auto kc) {
         constexpr int k0 = decltype(kc)::value * 8;
@@ -1132,8 +1156,11 @@ k_theta(double* Q, const double* __restrict__ I, const Real* __restrict__ Pown, 
         for (int i = 0; i < 8; ++i) qv[i] = (k0 + i < B) ? qc[(k0 + i < B ? k0 + i : 0) * kTile] : 0.0;
         static_for<0, 8>([&](auto ii) {
           constexpr int i = decltype(ii)::value;
-          if constexpr (k0 + i < B)
-            qc[(k0 + i) * kTile] = qv[i] + to_f64<Real, CVT>(row_dotr<N, 25 + sf, k0 + i, Real, BT>(T.val, Wr));
+          if constexpr (k0 + i < B) {
+            Real dq = row_dotr<N, 25 + f0, k0 + i, Real, BT>(T.val, Wr[0]);
+            if constexpr (FP == 2) dq += row_dotr<N, 25 + f0 + 1, k0 + i, Real, BT>(T.val, Wr[FP - 1]);
+            qc[(k0 + i) * kTile] = qv[i] + to_f64<Real, CVT>(dq);
+          }
         });
       });
     }
@@ -1240,12 +1267,14 @@ void ader_launch_small(const AderLaunch& L) {
 
 // Kernels of a 27-quantity step: WHICH 0 = k_local (VE, fused step), 1 = k_neigh on the
 // elastic rows (fused step), 2 = k_theta.
-// Shared memory of k_theta: operand rows outside the registers (as LocalRegRows: FP64
-// keeps C(N+2,3) rows in registers from degree 5 on) and the two face buffers.
+// Shared memory of k_theta: the volume's operand rows and exchange, then (aliased) the
+// staged projections of the faces of one pass.
 inline size_t ader_theta_smem(int N, bool f32) {
   const int B = (N + 1) * (N + 2) * (N + 3) / 6, BT = (N + 1) * (N + 2) / 2;
-  const int rs = (!f32 && N >= 5) ? (N + 2) * (N + 1) * N / 6 : B;
-  return (size_t)(f32 ? 4 : 8) * ((B - rs) + 2 * BT) * kNq * kTile;
+  const int KC = BT / 3 > 0 ? BT / 3 : 1;
+  const int fp = f32 ? ThetaFacesPerPass<float>::value : ThetaFacesPerPass<double>::value;
+  const int rows = (B + KC) > 2 * fp * BT ? (B + KC) : 2 * fp * BT;
+  return (size_t)(f32 ? 4 : 8) * rows * kNq * kTile;
 }
 template <int N, typename Real, int WHICH>
 void ader_set_attribute_ve(size_t smem) {
