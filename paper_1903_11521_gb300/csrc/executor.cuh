@@ -107,19 +107,23 @@ __device__ __forceinline__ Real ew_load(int kind, int ref, int off, const Real* 
 }
 
 // grid: any number of blocks of kEwWarps warps; dynamic shared memory kEwWarps *
-// temp_entries * sizeof(Real).
+// temp_entries * sizeof(Real) (GTMP: none; the temporaries in `scratch`, [warp][entries],
+// for plans whose temporaries exceed the shared-memory cap: each warp's slice stays in
+// L1 / L2 while the warp works on its element).
 constexpr int kEwWarps = 4;
 // plans whose four warps' temporaries fit this much shared memory use k_execute_ew (two
 // blocks per SM at least)
 constexpr int kEwSmemCap = 96 * 1024;
-template <typename Real>
+template <typename Real, bool GTMP = false>
 __global__ void __launch_bounds__(kEwWarps * 32)
 k_execute_ew(const ExecOp* __restrict__ ops, int nops, const int* __restrict__ prog,
-             const Real* __restrict__ consts, ExecPtrs<Real> T, int temp_entries, int64_t n_elements) {
+             const Real* __restrict__ consts, ExecPtrs<Real> T, int temp_entries, int64_t n_elements,
+             Real* __restrict__ scratch = nullptr) {
   extern __shared__ __align__(16) unsigned char ew_smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  Real* tmp = reinterpret_cast<Real*>(ew_smem) + (size_t)wib * temp_entries;
+  Real* tmp = GTMP ? scratch + ((size_t)blockIdx.x * kEwWarps + wib) * temp_entries
+                   : reinterpret_cast<Real*>(ew_smem) + (size_t)wib * temp_entries;
   const int64_t n_warps = (int64_t)gridDim.x * kEwWarps;
   for (int64_t e = (int64_t)blockIdx.x * kEwWarps + wib; e < n_elements; e += n_warps) {
     for (int o = 0; o < nops; ++o) {

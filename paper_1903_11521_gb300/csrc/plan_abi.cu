@@ -27,6 +27,7 @@ struct yt_plan {
   std::vector<int> slot_of_tensor;     // per-element tensor index -> pointer slot
   int temp_entries = 1;
   bool element_per_warp = false;       // executor kernel, chosen at creation
+  bool ew_global_temps = false;        // element per warp, temporaries in global scratch
   double nz_flops = 0, hw_flops = 0, naive_flops = 0;
   int64_t bytes_per_element = 0;
   int n_binary = 0;
@@ -212,14 +213,17 @@ void compile(yt_plan* p) {
     p->order += tp.order;
   }
   p->temp_entries = max_temp;
-  // kernel choice: one element per warp when four warps' temporaries fit in 96 KB of
-  // shared memory (two blocks per SM at least; with one block per SM the lane-per-element
-  // kernel was measured faster); its rows are then reordered by decreasing number of
-  // products (output entry order among equals), so that the lanes of a warp, which take
-  // consecutive rows, run similar numbers of products.  The lane-per-element kernel keeps
-  // the output entry order (its temporaries are written in that order).
+  // kernel choice: one element per warp, the temporaries in shared memory when four
+  // warps' temporaries fit in 96 KB (two blocks per SM at least), else in a global scratch
+  // slice per warp (16 warps per SM; with one block per SM and shared-memory temporaries it
+  // was slower than the lane-per-element kernel, with global ones 1.9x faster for the
+  // order-6 fused-simulation chain).  Rows are reordered by decreasing number of products
+  // (output entry order among equals), so that the lanes of a warp, which take
+  // consecutive rows, run similar numbers of products.  The lane-per-element kernel (the
+  // allocation-free entry point) reads the same rows in that order.
   const size_t word_bytes = p->prec == YT_F32 ? 4 : 8;
-  p->element_per_warp = (size_t)kEwWarps * p->temp_entries * word_bytes <= (size_t)kEwSmemCap;
+  p->element_per_warp = true;
+  p->ew_global_temps = (size_t)kEwWarps * p->temp_entries * word_bytes > (size_t)kEwSmemCap;
   if (p->element_per_warp) {
     for (const ExecOp& op : p->ops) {
       if (op.kind == kOpZero || op.nrows == 0) continue;
@@ -308,6 +312,29 @@ void launch(yt_plan* p, void* const* ptrs, int64_t n, cudaStream_t st) {
   cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
   // one element per warp with the temporaries in shared memory (kernel chosen at creation)
   const size_t ew_smem = (size_t)kEwWarps * p->temp_entries * sizeof(Real);
+  if (p->element_per_warp && p->ew_global_temps) {
+    // four blocks of four warps per SM, each warp's temporaries in its slice of the scratch
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + kEwWarps - 1) / kEwWarps,
+                                                                  (int64_t)sms * 4));
+    const size_t need = (size_t)blocks * kEwWarps * p->temp_entries * sizeof(Real);
+    std::lock_guard<std::mutex> lock(p->mu);
+    ensure_device<Real>(p);
+    if (p->scratch_bytes < need) {
+      if (p->scratch) {
+        cuda_check(cudaStreamSynchronize(st), "sync before scratch growth");
+        cudaFree(p->scratch);
+        p->scratch = nullptr;
+        p->scratch_bytes = 0;
+      }
+      cuda_check(cudaMalloc(&p->scratch, need), "cudaMalloc scratch");
+      p->scratch_bytes = need;
+    }
+    k_execute_ew<Real, true><<<(unsigned)blocks, kEwWarps * 32, 0, st>>>(
+        p->d_ops, (int)p->ops.size(), p->d_prog, static_cast<const Real*>(p->d_consts), T,
+        p->temp_entries, n, static_cast<Real*>(p->scratch));
+    cuda_check(cudaGetLastError(), "k_execute_ew launch");
+    return;
+  }
   if (p->element_per_warp) {
     std::lock_guard<std::mutex> lock(p->mu);
     ensure_device<Real>(p);

@@ -98,3 +98,70 @@ def test_full_size_step_sampled(order, prec_name, tol_q, tol_inc):
         parity.check(f"full size o{order} {prec_name} Q", got, ref, tol_q, tol_q)
     parity.check(f"full size o{order} {prec_name} dQ ({sample.size} sampled)", got, ref, tol_inc,
                  tol_el, base=q0)
+
+
+# ----------------------------------------------------------------- 27 quantities
+# The 27-quantity precision workload at its full size: order 7 on the jittered periodic
+# structured mesh of 55^3 x 6 = 998,250 tets, synthetic attenuation, the bench's seeds.
+VE_N = 55
+VE_ORDER = 7
+
+
+@functools.lru_cache(maxsize=1)
+def ve_case():
+    mesh = wl.jittered_periodic_mesh(VE_N, jitter=0.1, seed=wl.SEED + 800, length=100.0 * VE_N,
+                                     rho=2500.0, lam=2.5e10, mu=2.5e10)
+    el, conn = mesh.elements, mesh.conn
+    N = VE_ORDER - 1
+    dt = wl.cfl_time_step(el, N)
+    att = wl.attenuation(el, dt, seed=wl.SEED + 900)
+    Q = wl.random_dofs_viscoelastic(el.rho.size, basis.n_basis(N), el, att, seed=wl.SEED + 901)
+    rng = np.random.default_rng(11)
+    Ev = el.rho.size
+    sample = np.concatenate([[0, Ev - 1], rng.choice(Ev, N_SAMPLE - 2, replace=False)])
+    return el, conn, att, Q, dt, sample
+
+
+@functools.lru_cache(maxsize=1)
+def ve_reference():
+    """Q_new of the sampled elements from the 27-quantity oracle, evaluated for the sampled
+    elements and their neighbours only."""
+    from oracle import viscoelastic as ve
+    el, conn, att, Q, dt, sample = ve_case()
+    N = VE_ORDER - 1
+    ids = np.unique(np.concatenate([sample, conn.neighbours[sample].ravel()]))
+    star, src, loc, nb = ve.setup_element_matrices(el.rho[ids], el.lam[ids], el.mu[ids], att.ylam[ids],
+                                                   att.ymu[ids], att.omega[ids], el.jac[ids])
+    _, I = ve.derivatives_and_time_integral(Q[ids], star, src, dt, N)
+    pos = {int(g): i for i, g in enumerate(ids)}
+    rows = np.array([pos[int(g)] for g in sample])
+    out = ve.local_update(Q[sample], I[rows], star[rows], src[rows], loc[rows], N)
+    m = basis.float_matrices(N)
+    for r, g in enumerate(sample):
+        for s in range(4):
+            n = pos[int(conn.neighbours[g, s])]
+            F = m["FpHat"][s, conn.faces[g, s], conn.orient[g, s]]
+            out[r] = out[r] + F @ I[n] @ nb[rows[r], s].T
+    return out
+
+
+@pytest.mark.parametrize("prec_name", ["YT_F64", "YT_BF16X3_F32ACC"])
+def test_full_size_viscoelastic_step_sampled(prec_name):
+    import paper_1903_11521_gb300 as yt
+    el, conn, att, Q, dt, sample = ve_case()
+    ref = ve_reference()
+    mat = np.stack([el.rho, el.lam, el.mu], axis=1)
+    s = yt.Solver(VE_ORDER, dt, mat, el.jac, conn.neighbours, conn.faces, conn.orient,
+                  precision=getattr(yt, prec_name), attenuation=att)
+    s.set_dofs_host(Q)
+    s.step()
+    s.status()
+    got = s.get_host()[sample]
+    s.close()
+    if prec_name == "YT_F64":
+        parity.check(f"full size ve o7 {prec_name} Q", got, ref, parity.F64, parity.F64)
+        parity.check(f"full size ve o7 {prec_name} dQ ({sample.size} sampled)", got, ref, parity.F64_INC,
+                     parity.F64_INC, base=Q[sample])
+    else:
+        parity.check(f"full size ve o7 {prec_name} dQ ({sample.size} sampled)", got, ref, parity.VE_TC_INC,
+                     parity.VE_TC_INC_EL, base=Q[sample])
