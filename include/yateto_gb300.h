@@ -42,7 +42,7 @@ typedef enum yt_status {
   YT_ERR_INVALID = 1,      /* null pointer, out-of-range argument */
   YT_ERR_PARSE = 2,        /* malformed Einstein expression */
   YT_ERR_SHAPE = 3,        /* inconsistent index sizes / tensor dimensions */
-  YT_ERR_UNSUPPORTED = 4,  /* valid request that this build has no kernel for */
+  YT_ERR_UNSUPPORTED = 4,  /* valid request that the library has no kernel for */
   YT_ERR_OOM = 5,          /* device or host allocation failed */
   YT_ERR_CUDA = 6,         /* a CUDA runtime call failed (incl. no device) */
   YT_ERR_TIMEOUT = 7       /* a bounded device-side wait ran out */
