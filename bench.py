@@ -299,14 +299,31 @@ def form_precision(yt, order, E, steps, stream, precision="f32"):
     s.set_dofs_host(Q, stream=stream)
     ms = _timed(lambda: s.step(stream=stream), steps, 2, stream)
     s.status(stream=stream)
+    st = s.stats()
     s.close()
     out = {"workload": f"order {order}, {E} tets, {PRECISION_NAMES[precision]} contractions / "
                        f"FP64 setup, accumulation and DOFs",
            "value": E / (ms / 1e3), "unit": METRIC, "ms_per_step": ms}
+    # the step against the HBM roofline: algorithmic bytes (each stream once, the library's
+    # count) over the measured copy bandwidth
+    step_bytes = (st["local_bytes"] + st["neighbour_bytes"]) * E
+    gbs = step_bytes / (ms / 1e3) / 1e9
+    out["hbm"] = {"bytes_per_element": st["local_bytes"] + st["neighbour_bytes"], "achieved_gbs": gbs,
+                  "peak_gbs": measured_hbm_gbs(), "frac": gbs / measured_hbm_gbs(),
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth), of measured"}
     out["error_vs_fp64_increment"] = _increment_error(yt, order, code)
     out["error_definition"] = ("max over quantities of ||dQ - dQ_f64||_F / ||dQ_f64||_F, "
                                "one step, 20000 tets, against the FP64 path")
     return out
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth of the measured peaks file, else the fallback figure (6.8 TB/s)."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def mass_diagonal(yt, order):
