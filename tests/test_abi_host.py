@@ -53,6 +53,48 @@ def test_invalid_arguments_rejected_without_device(lib):
     assert lib.yt_step(None, None) == 1
 
 
+def _create_status(lib, E=4, order=4, dt=1e-3, precision=0, flags=0, quantities=0, neighbours=True,
+                   attenuation=False, n_halo=0):
+    """Status of yt_solver_create for a descriptor; every case below is rejected before any
+    device work (the argument checks come first), so no GPU is needed."""
+    n = min(E, 16)             # arrays of the cases that pass the count check; never read
+    mat = np.ones((n, 3))
+    jac = np.tile(np.eye(3).ravel(), (n, 1))
+    nb = np.zeros((n, 4), dtype=np.int32)
+    fj = np.zeros((n, 4), dtype=np.int8)
+    att = np.ones((n, 9))
+    mesh = _lib.MeshDesc(n_elements=E, material=mat.ctypes.data_as(C.POINTER(C.c_double)),
+                         jacobian=jac.ctypes.data_as(C.POINTER(C.c_double)), n_halo=n_halo)
+    if neighbours:
+        mesh.neighbours = nb.ctypes.data_as(C.POINTER(C.c_int32))
+        mesh.faces = fj.ctypes.data_as(C.POINTER(C.c_int8))
+        mesh.orient = fj.ctypes.data_as(C.POINTER(C.c_int8))
+    if attenuation:
+        mesh.attenuation = att.ctypes.data_as(C.POINTER(C.c_double))
+    sch = _lib.SchemeDesc(order=order, dt=dt, precision=precision, flags=flags, quantities=quantities)
+    out = C.c_void_p()
+    return lib.yt_solver_create(C.byref(mesh), C.byref(sch), None, C.byref(out))
+
+
+@pytest.mark.parametrize("case, status", [
+    (dict(E=1 << 24), 4),                                  # element index beyond the 24-bit packing
+    (dict(order=1), 1), (dict(order=8), 1),                # orders 2..7
+    (dict(dt=0.0), 1), (dict(dt=float("nan")), 1),
+    (dict(precision=7), 4),
+    (dict(flags=1), 1),                                    # diagnostics flag without the tensor cores
+    (dict(flags=2, precision=2), 1),                       # unknown flag
+    (dict(quantities=10), 1),
+    (dict(attenuation=True), 1),                           # attenuation on a 9-quantity solver
+    (dict(quantities=27), 1),                              # 27 quantities without attenuation
+    (dict(quantities=27, attenuation=True, neighbours=False), 1),
+    (dict(n_halo=-1), 1), (dict(n_halo=1 << 26), 1),
+    (dict(n_halo=8, precision=2), 4),                      # partitioned tensor-core solves
+    (dict(n_halo=8, quantities=27, attenuation=True), 4),  # partitioned 27-quantity solves
+])
+def test_solver_descriptor_limits_rejected_without_device(lib, case, status):
+    assert _create_status(lib, **case) == status, lib.yt_last_error()
+
+
 @pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
 def test_reference_matrices_match_oracle(order):
     N = order - 1
