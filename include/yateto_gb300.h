@@ -241,7 +241,9 @@ yt_status yt_solver_get(struct yt_solver* solver, yt_field field, double* out,
 yt_status yt_step(struct yt_solver* solver, yt_stream stream);
 /* Partial updates: yt_step_local applies derivatives, time integral, volume and local
  * flux (the complete local update); yt_step_neighbour then applies the neighbour flux.
- * Together they give the same result as yt_step up to rounding. */
+ * Together they give the same result as yt_step up to rounding.  A YT_F64 / YT_F32
+ * solver of orders 2..5 whose mesh has at most one tile of 32 elements per SM runs
+ * yt_step_local on CTAs of 8 elements (the same arithmetic, bitwise the same result). */
 yt_status yt_step_local(struct yt_solver* solver, yt_stream stream);
 yt_status yt_step_neighbour(struct yt_solver* solver, yt_stream stream);
 /* The two kernels of yt_step, one at a time (phase 0 then phase 1 == yt_step): phase 0
