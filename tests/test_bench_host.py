@@ -121,3 +121,14 @@ def test_elastic_energy_equals_quadrature_of_the_density():
     Mk = np.diag(basis.float_matrices(N)["M"])
     got = bench.elastic_energy(q, el, Mk, chunk=2)
     assert abs(got - ref) <= 1e-11 * abs(ref)
+
+
+def test_measured_hbm_peak_and_fallback(monkeypatch, tmp_path):
+    """The HBM denominator is the measured copy bandwidth of the peaks file when present,
+    else the fallback figure."""
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6781.8}')
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
+    assert bench.measured_hbm_gbs() == 6781.8
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
+    assert bench.measured_hbm_gbs() == 6800.0
