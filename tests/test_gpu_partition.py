@@ -29,7 +29,7 @@ def _free_port():
 
 
 def _inputs(kind):
-    if kind == "random":
+    if kind in ("random", "scattered"):
         E = 300
         el = wl.random_elements(E, seed=310)
         conn = wl.random_connectivity(E, seed=311)
@@ -42,6 +42,15 @@ def _inputs(kind):
     return el, conn, Q, dt
 
 
+def _owner(E, world, kind):
+    if kind == "scattered":
+        # every rank's elements spread over the mesh: the solver's own order differs from
+        # the global one, and most tiles have remote faces
+        return np.random.default_rng(314).permutation(np.arange(E) % world)
+    from paper_1903_11521_gb300 import partition
+    return partition.block_partition(E, world)
+
+
 def _rank(rank, world, port, kind, out_path):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -52,7 +61,7 @@ def _rank(rank, world, port, kind, out_path):
     import paper_1903_11521_gb300 as yt
     from paper_1903_11521_gb300 import partition
     el, conn, Q, dt = _inputs(kind)
-    owner = partition.block_partition(el.rho.size, world)
+    owner = _owner(el.rho.size, world, kind)
     ps = partition.PartitionedSolver(ORDER, dt, el, conn, owner, rank, dist, precision=yt.YT_F64,
                                      staging="host")
     ps.set_dofs(Q)
@@ -75,7 +84,7 @@ def _rank(rank, world, port, kind, out_path):
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("kind", ["random", "structured"])
+@pytest.mark.parametrize("kind", ["random", "structured", "scattered"])
 def test_two_rank_partitioned_step(tmp_path, kind):
     import paper_1903_11521_gb300 as yt
     out = str(tmp_path / "full.npy")

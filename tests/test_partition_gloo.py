@@ -1,5 +1,5 @@
-"""Host logic of the partitioned step (paper_1903_11521_gb300.partition) with two gloo
-ranks on CPU: each rank computes its elements' face projections, exchanges the remote
+"""Host logic of the partitioned step (paper_1903_11521_gb300.partition) with two and three
+gloo ranks on CPU, element blocks and scattered owners: each rank computes its elements' face projections, exchanges the remote
 ones, applies the neighbour flux with local + halo projections, and the gathered result
 equals the oracle's single-process step.  The per-element arithmetic here uses the
 oracle's factorised matrices (this is a test of the partition and exchange logic)."""
@@ -33,14 +33,21 @@ def _inputs():
     return el, conn, Q, dt, star, loc, nb
 
 
-def _rank(rank, world, port, out_path):
+def _owner(world, kind):
+    if kind == "block":
+        return partition.block_partition(E, world)
+    # scattered owners: every rank's elements spread over the mesh
+    return np.random.default_rng(303 + world).permutation(np.arange(E) % world)
+
+
+def _rank(rank, world, port, out_path, kind="block"):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=world)
     el, conn, Q, dt, star, loc, nb = _inputs()
     m = basis.float_matrices(ORDER_N)
-    owner = partition.block_partition(E, world)
+    owner = _owner(world, kind)
     plan = partition.halo_plan(owner, conn.neighbours, conn.faces, rank)
     mine = plan.local
     # local phase of the own elements
@@ -67,9 +74,10 @@ def _rank(rank, world, port, out_path):
     dist.destroy_process_group()
 
 
-def test_halo_plan_is_consistent():
+@pytest.mark.parametrize("kind", ["block", "scattered"])
+def test_halo_plan_is_consistent(kind):
     _, conn, _, _, _, _, _ = _inputs()
-    owner = partition.block_partition(E, 3)
+    owner = _owner(3, kind)
     plans = [partition.halo_plan(owner, conn.neighbours, conn.faces, r) for r in range(3)]
     for r, p in enumerate(plans):
         for peer, lst in p.recv.items():
@@ -81,9 +89,10 @@ def test_halo_plan_is_consistent():
 
 
 @pytest.mark.timeout(300)
-def test_two_rank_step_equals_single_process(tmp_path):
+@pytest.mark.parametrize("world, kind", [(2, "block"), (3, "scattered")])
+def test_multi_rank_step_equals_single_process(tmp_path, world, kind):
     out = str(tmp_path / "full.npy")
-    mp.start_processes(_rank, args=(2, _free_port(), out), nprocs=2, join=True,
+    mp.start_processes(_rank, args=(world, _free_port(), out, kind), nprocs=world, join=True,
                        start_method="spawn")
     full = np.load(out)
     el, conn, Q, dt, star, loc, nb = _inputs()
