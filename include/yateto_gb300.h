@@ -253,7 +253,8 @@ yt_status yt_step_neighbour(struct yt_solver* solver, yt_stream stream);
 yt_status yt_step_phase(struct yt_solver* solver, int32_t phase, yt_stream stream);
 /* One step (as yt_step) on host buffers: Q is read from `dofs_in` and the new Q written to
  * `dofs_out` (host memory, canonical layout; they may be the same buffer).  The transfers
- * are pipelined with the kernels in 8 element chunks on an internal copy stream: the
+ * are pipelined with the kernels in up to 16 element chunks (each a whole number of
+ * waves of one CTA per SM where the mesh allows) on an internal copy stream: the
  * upload of a chunk overlaps the local kernel of the previous one, and the download of a
  * chunk overlaps the neighbour kernel of the next one (the neighbour kernel of any chunk
  * needs the local results of all chunks).  Host buffers should be pinned for the copies

@@ -190,7 +190,7 @@ def test_phases_equal_step_and_unfused_path(yt):
 @pytest.mark.parametrize("E", [8 * 32 * 3 + 45, 512 * 32 + 77])
 @pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32", "YT_BF16X3_F32ACC"])
 def test_step_host_equals_step(yt, prec_name, E):
-    """yt_step_host (pipelined copies, 8 element chunks, ragged last chunk and tile; 26 and
+    """yt_step_host (pipelined copies, up to 16 element chunks, ragged last chunk and tile; 26 and
     515 tiles) gives bitwise the result of set_dofs + yt_step + get on the same solver;
     also in place."""
     import torch

@@ -95,7 +95,7 @@ def test_ve_bf16x3_step_against_oracle(yt, order):
 
 @pytest.mark.parametrize("prec_name", ["YT_F64", "YT_F32", "YT_BF16X3_F32ACC"])
 def test_ve_phases_and_host_step_equal_step(yt, prec_name):
-    """yt_step == phase 0 + phase 1 and == yt_step_host (8 element chunks, ragged last
+    """yt_step == phase 0 + phase 1 and == yt_step_host (element chunks, ragged last
     chunk and tile) bitwise."""
     import torch
     prec = getattr(yt, prec_name)
