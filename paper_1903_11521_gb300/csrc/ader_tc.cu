@@ -122,7 +122,7 @@ void launch_local(const tc::TcLaunch& L) {
   float* P = L.Pface + (size_t)L.tile0 * kTile * 4 * kNq * tc::Layout<N>::BT8;
   tc::k_local_tc<N><<<L.grid, tc::kRows, tc::Layout<N>::SMEM, L.stream>>>(
       L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, step_of(L), L.SP, VeTables<float>{},
-      L.ntiles, L.status);
+      L.vol, L.ntiles, L.status);
 }
 
 template <int N>
@@ -130,13 +130,13 @@ void launch_neigh(const tc::TcLaunch& L, int variant) {
   const size_t sm = tc::Layout<N>::SMEM_N;
   if (variant == 0)
     tc::k_neigh_tc<N, true, true><<<L.grid, tc::kRows, sm, L.stream>>>(
-        L.Q, L.Pface, L.Wloc, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
+        L.Q, L.Pface, L.Wloc, L.vol, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
   else if (variant == 1)
     tc::k_neigh_tc<N, false, true><<<L.grid, tc::kRows, sm, L.stream>>>(
-        L.Q, L.Pface, L.Wloc, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
+        L.Q, L.Pface, L.Wloc, L.vol, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
   else
     tc::k_neigh_tc<N, true, false><<<L.grid, tc::kRows, sm, L.stream>>>(
-        L.Q, L.Pface, L.Wloc, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
+        L.Q, L.Pface, L.Wloc, L.vol, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
 }
 
 }  // namespace

@@ -387,9 +387,12 @@ __device__ __forceinline__ void cp_async16(float* dst_shared, const float* src_g
 // ------------------------------------------------------------------------- K_local
 // Derivatives, time integral, volume, face projections and local flux products of tiles
 // of 32 elements; persistent CTAs (grid <= number of tiles) stride over the tiles.
-// Outputs and layouts as k_local<N, false, float>: Q (volume added), I, Wloc
-// [tile][4][9][BT][32] = (R^sT I) Aloc_s^T, except that the face projections Pface are
-// [element][4][9][BT8] (rows padded to 8 floats: 16-byte copies in k_neigh_tc).
+// Outputs and layouts as k_local<N, false, float>: I, Wloc [tile][4][9][BT][32] =
+// (R^sT I) Aloc_s^T, except that the face projections Pface are [element][4][9][BT8] (rows
+// padded to 8 floats: 16-byte copies in k_neigh_tc) and that the volume increment is not
+// added to Q here but written to Vol [tile][9][B][32] (binary32): k_neigh_tc adds it with
+// the lifting in one binary64 update of Q (one read-modify-write of Q per step instead
+// of two).  VE: Q gets the volume and the stress rows' source here.
 // The scaled derivatives D~^d (binary32, as produced) go to this CTA's scratch rows
 // [SROWS][9][32] (L2-resident, reused tile after tile); the time integral is summed from
 // them in binary64, in the order d = 0..N, once the derivatives are done.  Keeping the
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(kRows, 1)
 k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, float* __restrict__ Wloc,
            const float* __restrict__ star, const float* __restrict__ floc,
            const unsigned char* __restrict__ blob, float* __restrict__ scratch, TcStep T, StarPattern SP,
-           VeTables<float> V, int64_t ntiles, int* __restrict__ status) {
+           VeTables<float> V, float* __restrict__ Vol, int64_t ntiles, int* __restrict__ status) {
   using L = Layout<N>;
   using Dm = Dims<N>;
   constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPA = L::KPA, NI = L::NI, CS = L::CS, NV = L::NV;
@@ -876,19 +879,24 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       constexpr int R = L::vrows(V), R8 = up8(R), KB0 = V * L::VR;
       wait_pass(L::ND + V + 1);       // the next volume pass or the face projections
       uint32_t ua[24], ub[24];
-      double qa[8], qb[8];           // Q of chunk c in qa (c even) or qb (c odd), loaded one chunk ahead
+      double qa[8], qb[8];           // VE: Q of chunk c in qa (c even) or qb (c odd), loaded one chunk ahead
       load_chunk(0, R8, ua);
+      if constexpr (VE) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) qa[i] = (i < R) ? Qt[(w * B + KB0 + (i < R ? i : 0)) * kTile + lane] : 0.0;
+        for (int i = 0; i < 8; ++i) qa[i] = (i < R) ? Qt[(w * B + KB0 + (i < R ? i : 0)) * kTile + lane] : 0.0;
+      }
+      float* Vt = VE ? nullptr : Vol + tile * (kNq * B * kTile);
       static_for<0, R8 / 8>([&](auto cc) {
         constexpr int c = decltype(cc)::value, k0 = c * 8;
         auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24], double (&qc)[8], double (&qn)[8]) {
           put_chunk(cur);
           if constexpr (k0 + 8 < R8) {
             load_chunk(k0 + 8, R8, nxt);
+            if constexpr (VE) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              qn[i] = (k0 + 8 + i < R) ? Qt[(w * B + KB0 + (k0 + 8 + i < R ? k0 + 8 + i : 0)) * kTile + lane] : 0.0;
+              for (int i = 0; i < 8; ++i)
+                qn[i] = (k0 + 8 + i < R) ? Qt[(w * B + KB0 + (k0 + 8 + i < R ? k0 + 8 + i : 0)) * kTile + lane] : 0.0;
+            }
           }
           __syncthreads();
           float v[8];
@@ -905,7 +913,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
                 }
                 Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]) + src;
               } else {
-                Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]);
+                Vt[(w * B + k) * kTile + lane] = v[i];
               }
             }
           }
@@ -994,8 +1002,9 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
 template <int N, bool WITH_LOCAL, bool WITH_NEIGH, int NQT = kNq>
 __global__ void __launch_bounds__(kRows, 1)
 k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__ Wloc,
-           const float* __restrict__ fnb, const int* __restrict__ conn, const float* __restrict__ fmat,
-           const unsigned char* __restrict__ blob, int64_t ntiles, int* __restrict__ status) {
+           const float* __restrict__ Vol, const float* __restrict__ fnb, const int* __restrict__ conn,
+           const float* __restrict__ fmat, const unsigned char* __restrict__ blob, int64_t ntiles,
+           int* __restrict__ status) {
   using L = Layout<N>;
   constexpr int B = L::B, BT = L::BT, BT8 = L::BT8, KPN = L::KPN, NPL = L::NPL, KPE = L::KPE;
   constexpr int NM4 = L::LIFT2 ? (BT + 3) / 4 : BT8 / 4;        // float4 rows of the exchange
@@ -1155,13 +1164,22 @@ k_neigh_tc(double* Q, const float* __restrict__ Pface, const float* __restrict__
     issue_lift(L::LIFT2 ? 1 : 0);
     wait_lift();
     double* Qt = Q + tile * (NQT * B * kTile);
+    // WITH_LOCAL (9 quantities): the local kernel's volume increment joins the lifting in
+    // the one binary64 update of Q
+    constexpr bool ADD_VOL = WITH_LOCAL && NQT == kNq;
+    const float* Vt = ADD_VOL ? Vol + tile * (kNq * B * kTile) : nullptr;
     static_for<0, up8(B) / 8>([&](auto cc) {
       constexpr int k0 = decltype(cc)::value * 8;
+      float vv[8];
+      if constexpr (ADD_VOL) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) vv[i] = (k0 + i < B) ? __ldg(Vt + (w * B + (k0 + i < B ? k0 + i : 0)) * kTile + lane) : 0.0f;
+      }
       float r[8];
       tmem_ld8(my_tmem + k0, r);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        if (k0 + i < B) Qt[(w * B + k0 + i) * kTile + lane] += f2d_int(r[i]);
+        if (k0 + i < B) Qt[(w * B + k0 + i) * kTile + lane] += f2d_int(ADD_VOL ? r[i] + vv[i] : r[i]);
     });
     fence_before_sync();
     __syncthreads();
@@ -1187,6 +1205,7 @@ struct TcLaunch {
   const int* conn;
   const unsigned char *blob_local, *blob_neigh;
   float* scratch;            // grid x Layout<N>::SROWS x 288 floats
+  float* vol;                // [tile][9][B][32] volume increments (9-quantity steps)
   VeTables<float> ve;        // 27-quantity steps: anelastic scratch, star rows, rates
   double dt;
   StarPattern SP;

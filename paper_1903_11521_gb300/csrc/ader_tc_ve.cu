@@ -20,14 +20,14 @@ template <int N>
 void launch_local_ve(const tc::TcLaunch& L) {
   float* P = L.Pface + (size_t)L.tile0 * kTile * 4 * kNq * tc::Layout<N>::BT8;
   tc::k_local_tc<N, true><<<L.grid, tc::kRows, tc::Layout<N>::SMEM, L.stream>>>(
-      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, tc_step_of(L), L.SP, L.ve, L.ntiles,
-      L.status);
+      L.Q, L.I, P, L.Wloc, L.star, L.floc, L.blob_local, L.scratch, tc_step_of(L), L.SP, L.ve, nullptr,
+      L.ntiles, L.status);
 }
 
 template <int N>
 void launch_neigh_ve(const tc::TcLaunch& L) {
   tc::k_neigh_tc<N, true, true, kNqVe><<<L.grid, tc::kRows, tc::Layout<N>::SMEM_N, L.stream>>>(
-      L.Q, L.Pface, L.Wloc, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
+      L.Q, L.Pface, L.Wloc, nullptr, L.fnb, L.conn, L.f, L.blob_neigh, L.ntiles, L.status);
 }
 
 }  // namespace

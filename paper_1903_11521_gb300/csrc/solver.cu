@@ -486,6 +486,7 @@ tc::TcLaunch tc_args(yt_solver* s, cudaStream_t st, int64_t t0 = 0, int64_t nt =
   L.conn = s->conn + e0 * 4;
   L.blob_local = s->d_tc_local;
   L.scratch = s->d_tc_scratch;
+  L.vol = s->d_tc_vol ? s->d_tc_vol + e0 * kNq * s->B : nullptr;
   L.blob_neigh = s->d_tc_neigh;
   L.ve = VeTables<float>{};
   if (s->P == kNqVe) {
@@ -721,6 +722,7 @@ void build_tables(yt_solver* s) {
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
     s->tc_grid = (unsigned)std::min<int64_t>(s->ntiles, sms);
     s->d_tc_scratch = dalloc<float>(tc_scratch_floats(N, s->tc_grid));
+    if (s->P == kNq) s->d_tc_vol = dalloc<float>((size_t)s->Epad * kNq * s->B);
     if (s->P == kNqVe) {
       // k_theta (FP32): its sparse lists' values, from constant memory too at degree <= 5
       std::vector<float> v32(csr.val.begin(), csr.val.end());

@@ -35,6 +35,7 @@ struct yt_solver {
   float* d_tc_scratch = nullptr;
   int* d_status = nullptr;
   unsigned tc_grid = 0;
+  float* d_tc_vol = nullptr;  // tensor-core form: volume increments [tile][9][B][32]
   bool small_local = false;   // yt_step_local on the small-mesh kernel (tiles <= SMs)
   bool diag_expire_wait = false;     // YT_SCHEME_DIAG_EXPIRE_WAIT
   // 27 quantities: anelastic star slots, relaxation frequencies and flux-solver rows (FP64
@@ -75,7 +76,7 @@ struct yt_solver {
     for (void* p : {(void*)Q, (void*)I, Pface, Wloc, (void*)star, (void*)floc, (void*)fnb, star_r,
                     floc_r, fnb_r, (void*)staging, (void*)conn, (void*)d_val, (void*)d_f,
                     (void*)d_val32, (void*)d_f32, (void*)d_tc_local, (void*)d_tc_neigh, (void*)d_tc_scratch,
-                    (void*)d_status})
+                    (void*)d_tc_vol, (void*)d_status})
       free_device(p);
   }
 };
