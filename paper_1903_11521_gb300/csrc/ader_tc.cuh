@@ -176,6 +176,10 @@ struct Layout {
   // k_local_tc converts with the integer units (fp_convert.cuh) except at degree 5, where
   // the extra registers cost more than the FP64-pipe slots they save (measured)
   static constexpr bool INT_CVT_LOCAL = N <= 4;
+  // the time integral widens its binary32 derivative terms on the integer units at every
+  // degree (measured at order 6: k_local_tc 14.4 -> 13.1 ms; narrowing I or Q the same
+  // way was slower: 15.5 / 16.5 ms)
+  static constexpr bool INT_WIDEN_TI = true;
   static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
   static_assert(BT8 / 8 <= XS_CHUNKS, "face basis too large for the exchange buffer");
   static_assert(SMEM <= kSmemCap && SMEM_N <= kSmemCap, "shared memory of one CTA exceeded");
@@ -861,7 +865,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
           double ik = dt * T.invfact[0] * qv[i];
 #pragma unroll
           for (int d = 1; d <= N; ++d)
-            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], to_f64<float, L::INT_CVT_LOCAL>(sv[d - 1][i]), ik);
+            if (k < Dm::nd(d)) ik = fma(dt * T.invfact[d], to_f64<float, L::INT_WIDEN_TI>(sv[d - 1][i]), ik);
           It[(w * B + k) * kTile + lane] = ik;
           v[i] = from_f64<float, L::INT_CVT_LOCAL>(ik);
         } else {
