@@ -184,3 +184,85 @@ def test_result_pattern_block_product():
     assert np.array_equal(es.result_pattern('ij', [('ik', D), ('kj', X)]), X)
     # an all-false operand gives an all-false result
     assert not es.result_pattern('ij', [('ik', D), ('kj', np.zeros((4, 4), dtype=bool))]).any()
+
+
+def _tree_leaves(t):
+    if isinstance(t, str):
+        return [t]
+    if t[0] == 'sum':
+        return _tree_leaves(t[2])
+    return _tree_leaves(t[1]) + _tree_leaves(t[2])
+
+
+def _evaluate_tree(out_idx, operands, tree, names, early=True):
+    """Values of a binary tree: each '*' node is the pairwise product over the union of
+    its children's indices (numpy.einsum), each 'sum' node sums exactly the indices it
+    names.  With early=True a '*'-only tree also sums, after each product, every index
+    that neither the result nor an operand outside the subtree carries."""
+    lookup = dict(zip(names, operands))
+
+    def ev(t):
+        if isinstance(t, str):
+            idx, arr = lookup[t]
+        elif t[0] == 'sum':
+            cidx, carr = ev(t[2])
+            assert set(t[1]) <= set(cidx)
+            idx = ''.join(c for c in cidx if c not in t[1])
+            return idx, np.einsum(f'{cidx}->{idx}', carr)
+        else:
+            li, la = ev(t[1])
+            ri, ra = ev(t[2])
+            idx = li + ''.join(c for c in ri if c not in li)
+            arr = np.einsum(f'{li},{ri}->{idx}', la, ra)
+        if early:
+            used = _tree_leaves(t)
+            keep = set(out_idx).union(*(set(lookup[n][0]) for n in names if n not in used))
+            nidx = ''.join(c for c in idx if c in keep)
+            if nidx != idx:
+                arr = np.einsum(f'{idx}->{nidx}', arr)
+                idx = nidx
+        return idx, arr
+
+    idx, arr = ev(tree)
+    assert set(idx) == set(out_idx)
+    return np.einsum(f'{idx}->{out_idx}', arr)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_every_contraction_order_gives_the_same_values(seed):
+    """Sec. 4.3: strength reduction only reorders an exact sum of products, so every
+    binary tree (with early summation) evaluates Eq. gentensorop to rounding, and so does
+    the tree the subset search returns, evaluated by its own 'sum' nodes alone (a sum
+    placed before an operand that still carries the index would change the values)."""
+    rng = np.random.default_rng(200 + seed)
+    sizes = {'a': 3, 'b': 2, 'c': 3, 'd': 2, 'e': 2}
+    specs = ['ab', 'bc', 'cd', 'de', 'ea']
+    vals = [rng.standard_normal([sizes[c] for c in s]) * (rng.random([sizes[c] for c in s]) < 0.7)
+            for s in specs]
+    ops = list(zip(specs, vals))
+    names = [f'T{i}' for i in range(5)]
+    ref = es.einsum_bruteforce('ac', ops)
+    scale = es.einsum_bruteforce('ac', [(s, np.abs(v)) for s, v in ops]).max()
+    trees = list(_all_trees(names))
+    assert len(trees) == 105                                  # (2n - 3)!! for n = 5
+    for t in trees:
+        got = _evaluate_tree('ac', ops, t, names)
+        assert np.abs(got - ref).max() <= 1e-14 * scale
+    _, best = es.strength_reduce('ac', [(s, v != 0) for s, v in ops], names)
+    got = _evaluate_tree('ac', ops, best, names, early=False)
+    assert np.abs(got - ref).max() <= 1e-14 * scale
+
+
+def test_madness_tree_values():
+    """The tree the search returns for the low-rank separated operator of Sec. 7 (rank 2,
+    p = 3) evaluates, by its own 'sum' nodes, to Eq. gentensorop."""
+    rng = np.random.default_rng(7)
+    specs = ['xyz', 'xl', 'li', 'ym', 'mj', 'zn', 'nk']
+    names = ['S', 'XL', 'XR', 'YL', 'YR', 'ZL', 'ZR']
+    shp = {'x': 3, 'y': 3, 'z': 3, 'i': 3, 'j': 3, 'k': 3, 'l': 2, 'm': 2, 'n': 2}
+    ops = [(s, rng.standard_normal([shp[c] for c in s])) for s in specs]
+    _, tree = es.strength_reduce('ijk', [(s, np.ones(v.shape, bool)) for s, v in ops], names)
+    ref = es.einsum_bruteforce('ijk', ops)
+    scale = es.einsum_bruteforce('ijk', [(s, np.abs(v)) for s, v in ops]).max()
+    got = _evaluate_tree('ijk', ops, tree, names, early=False)
+    assert np.abs(got - ref).max() <= 1e-14 * scale
