@@ -180,6 +180,12 @@ struct Layout {
   // degree (measured at order 6: k_local_tc 14.4 -> 13.1 ms; narrowing I or Q the same
   // way was slower: 15.5 / 16.5 ms)
   static constexpr bool INT_WIDEN_TI = true;
+  // the 8-row chunk loops of k_local_tc's volume mixing and face projections run as
+  // loops (one copy of the body per chunk parity) instead of fully unrolled: at order 7
+  // the unrolled kernel waits on instruction fetch first (measured at 1M tets: 25.2 ->
+  // 23.8 ms).  The derivative mixing stays unrolled: as a loop it spills (ptxas: 132 ->
+  // 320 bytes of spill stores), which cost what the smaller code saved (25.3 ms).
+  static constexpr bool ROLL = N >= 6;
   static_assert(3 * CS <= 512 && 3 * NPL <= 512, "accumulators exceed tensor memory");
   static_assert(BT8 / 8 <= XS_CHUNKS, "face basis too large for the exchange buffer");
   static_assert(SMEM <= kSmemCap && SMEM_N <= kSmemCap, "shared memory of one CTA exceeded");
@@ -310,6 +316,36 @@ __device__ __forceinline__ void store_split8(unsigned char* op, int split_bytes,
   }
   *reinterpret_cast<uint4*>(op + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   *reinterpret_cast<uint4*>(op + split_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// Calls body(k0, odd) for the 8-row chunks k0 = 0, 8, .., 8 (NCH - 1) of a pass, odd =
+// integral_constant<bool, chunk index odd>, so that the body picks its double-buffered
+// register arrays at compile time.  ROLL: a loop over chunk pairs (one copy of the body
+// per parity), else fully unrolled (k0 folds to a constant).
+template <int NCH, bool ROLL, typename F>
+__device__ __forceinline__ void for_chunk_pairs(F&& body) {
+  if constexpr (ROLL && NCH > 2) {
+#pragma unroll 1
+    for (int c = 0; c < NCH; c += 2) {
+      body(8 * c, std::false_type{});
+      if (c + 1 < NCH) body(8 * c + 8, std::true_type{});
+    }
+  } else {
+    static_for<0, NCH>([&](auto cc) {
+      constexpr int c = decltype(cc)::value;
+      body(8 * c, std::integral_constant<bool, (c & 1) != 0>{});
+    });
+  }
+}
+// Calls body(c) for c = 0 .. NC - 1: a loop (ROLL) or fully unrolled.
+template <int NC, bool ROLL, typename F>
+__device__ __forceinline__ void for_chunks(F&& body) {
+  if constexpr (ROLL && NC > 1) {
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) body(c);
+  } else {
+    static_for<0, NC>([&](auto cc) { body((int)decltype(cc)::value); });
+  }
 }
 
 // The MMAs of one pass for accumulator group g (K steps of 16 x three products), issued
@@ -629,29 +665,26 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       constexpr int DELTA = tc_delta<N>(P), R = tc_rows<N>(P), R8 = up8(R), ROW0 = tc_row0<N>(P);
       uint32_t ua[24], ub[24];       // chunk c in ua (c even) or ub (c odd)
       load_chunk(0, R8, ua);
-      static_for<0, R8 / 8>([&](auto cc) {
-        constexpr int c = decltype(cc)::value, k0 = c * 8;
-        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24]) {
-          put_chunk(cur);
-          if constexpr (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
-          __syncthreads();
-          float v[8];
-          mix_star(sc, v);
+      for_chunk_pairs<R8 / 8, false>([&](int k0, auto odd) {
+        uint32_t (&cur)[24] = decltype(odd)::value ? ub : ua;
+        uint32_t (&nxt)[24] = decltype(odd)::value ? ua : ub;
+        put_chunk(cur);
+        if (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
+        __syncthreads();
+        float v[8];
+        mix_star(sc, v);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = k0 + i;
-            if (k < R) {
-              v[i] *= dtf;
-              my_scr[(tc_srow<N>(DELTA + 1) + ROW0 + k) * kRows] = v[i];
-            } else {
-              v[i] = 0.0f;
-            }
+        for (int i = 0; i < 8; ++i) {
+          const int k = k0 + i;
+          if (k < R) {
+            v[i] *= dtf;
+            my_scr[(tc_srow<N>(DELTA + 1) + ROW0 + k) * kRows] = v[i];
+          } else {
+            v[i] = 0.0f;
           }
-          if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
-          if constexpr (k0 + 8 < R8) __syncthreads();
-        };
-        if constexpr (c % 2 == 0) body(ua, ub);
-        else body(ub, ua);
+        }
+        if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
+        if (k0 + 8 < R8) __syncthreads();
       });
     };
     // VE: the anelastic functions of the 8 rows kb..kb+7 of stress warp w and the source
@@ -711,38 +744,35 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       constexpr int R = tc_rows<N>(PB), R8 = up8(R), ROW0 = tc_row0<N>(PB);
       uint32_t ua[24], ub[24];
       load_chunk(0, R8, ua);
-      static_for<0, R8 / 8>([&](auto cc) {
-        constexpr int c = decltype(cc)::value, k0 = c * 8;
-        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24]) {
-          put_chunk(cur);
-          if constexpr (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
-          // I of this chunk's rows, loaded ahead of the anelastic stores
-          double iv[8];
+      for_chunk_pairs<R8 / 8, false>([&](int k0, auto odd) {
+        uint32_t (&cur)[24] = decltype(odd)::value ? ub : ua;
+        uint32_t (&nxt)[24] = decltype(odd)::value ? ua : ub;
+        put_chunk(cur);
+        if (k0 + 8 < R8) load_chunk(k0 + 8, R8, nxt);
+        // I of this chunk's rows, loaded ahead of the anelastic stores
+        double iv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = ROW0 + k0 + i;
-            iv[i] = (k < B) ? It[(w * B + (k < B ? k : 0)) * kTile + lane] : 0.0;
-          }
-          __syncthreads();
-          float v[8];
-          mix_star(sc, v);
-          if (w < 6) ve_chunk(ROW0 + k0, v, cw, std::true_type{});
+        for (int i = 0; i < 8; ++i) {
+          const int k = ROW0 + k0 + i;
+          iv[i] = (k < B) ? It[(w * B + (k < B ? k : 0)) * kTile + lane] : 0.0;
+        }
+        __syncthreads();
+        float v[8];
+        mix_star(sc, v);
+        if (w < 6) ve_chunk(ROW0 + k0, v, cw, std::true_type{});
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = ROW0 + k0 + i;
-            if (k < B) {
-              v[i] *= dtf;
-              It[(w * B + k) * kTile + lane] = fma(cw, to_f64<float, L::INT_CVT_LOCAL>(v[i]), iv[i]);
-              if constexpr (!TO_OPA) my_scr[(ROW0 + k0 + i) * kRows] = v[i];
-            } else {
-              v[i] = 0.0f;
-            }
+        for (int i = 0; i < 8; ++i) {
+          const int k = ROW0 + k0 + i;
+          if (k < B) {
+            v[i] *= dtf;
+            It[(w * B + k) * kTile + lane] = fma(cw, to_f64<float, L::INT_CVT_LOCAL>(v[i]), iv[i]);
+            if constexpr (!TO_OPA) my_scr[(ROW0 + k0 + i) * kRows] = v[i];
+          } else {
+            v[i] = 0.0f;
           }
-          if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
-          if constexpr (k0 + 8 < R8) __syncthreads();
-        };
-        if constexpr (c % 2 == 0) body(ua, ub);
-        else body(ub, ua);
+        }
+        if constexpr (TO_OPA) store_split8(opa, L::OPA_SPLIT, op_offset(my_row, ROW0 + k0, KPA), v);
+        if (k0 + 8 < R8) __syncthreads();
       });
     };
 
@@ -890,41 +920,41 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
         for (int i = 0; i < 8; ++i) qa[i] = (i < R) ? Qt[(w * B + KB0 + (i < R ? i : 0)) * kTile + lane] : 0.0;
       }
       float* Vt = VE ? nullptr : Vol + tile * (kNq * B * kTile);
-      static_for<0, R8 / 8>([&](auto cc) {
-        constexpr int c = decltype(cc)::value, k0 = c * 8;
-        auto body = [&](uint32_t (&cur)[24], uint32_t (&nxt)[24], double (&qc)[8], double (&qn)[8]) {
-          put_chunk(cur);
-          if constexpr (k0 + 8 < R8) {
-            load_chunk(k0 + 8, R8, nxt);
+      for_chunk_pairs<R8 / 8, L::ROLL>([&](int k0, auto odd) {
+        constexpr bool ODD = decltype(odd)::value;
+        uint32_t (&cur)[24] = ODD ? ub : ua;
+        uint32_t (&nxt)[24] = ODD ? ua : ub;
+        double (&qc)[8] = ODD ? qb : qa;
+        double (&qn)[8] = ODD ? qa : qb;
+        put_chunk(cur);
+        if (k0 + 8 < R8) {
+          load_chunk(k0 + 8, R8, nxt);
+          if constexpr (VE) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              qn[i] = (k0 + 8 + i < R) ? Qt[(w * B + KB0 + (k0 + 8 + i < R ? k0 + 8 + i : 0)) * kTile + lane] : 0.0;
+          }
+        }
+        __syncthreads();
+        float v[8];
+        mix_star(sc, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = KB0 + k0 + i;
+          if (k0 + i < R) {
             if constexpr (VE) {
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                qn[i] = (k0 + 8 + i < R) ? Qt[(w * B + KB0 + (k0 + 8 + i < R ? k0 + 8 + i : 0)) * kTile + lane] : 0.0;
-            }
-          }
-          __syncthreads();
-          float v[8];
-          mix_star(sc, v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = KB0 + k0 + i;
-            if (k0 + i < R) {
-              if constexpr (VE) {
-                double src = 0.0;                // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
-                if (w < 6) {
-                  const double* ith = It + ((size_t)(9 + w) * B + k) * kTile + lane;
-                  src = -((ith[0] + ith[LS]) + ith[2 * LS]);
-                }
-                Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]) + src;
-              } else {
-                Vt[(w * B + k) * kTile + lane] = v[i];
+              double src = 0.0;                // (I E^T)_{k, sigma_i} = -sum_l I[k][theta^l_i]
+              if (w < 6) {
+                const double* ith = It + ((size_t)(9 + w) * B + k) * kTile + lane;
+                src = -((ith[0] + ith[LS]) + ith[2 * LS]);
               }
+              Qo[(w * B + k) * kTile + lane] = qc[i] + to_f64<float, L::INT_CVT_LOCAL>(v[i]) + src;
+            } else {
+              Vt[(w * B + k) * kTile + lane] = v[i];
             }
           }
-          if constexpr (k0 + 8 < R8) __syncthreads();
-        };
-        if constexpr (c % 2 == 0) body(ua, ub, qa, qb);
-        else body(ub, ua, qb, qa);
+        }
+        if (k0 + 8 < R8) __syncthreads();
       });
       fence_before_sync();
       __syncthreads();
@@ -944,8 +974,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
     float* Wt = Wloc + tile * (4 * kNq * BT * kTile);
     static_for<0, 4>([&](auto face) {
       constexpr int s = decltype(face)::value;
-      static_for<0, BT8 / 8>([&](auto cc) {
-        constexpr int c = decltype(cc)::value;
+      for_chunks<BT8 / 8, L::ROLL>([&](int c) {
         float r[8];
         tmem_ld8(my_tmem + s * BT8 + 8 * c, r);
         float4* pe = reinterpret_cast<float4*>(Pe + (s * kNq + w) * BT8 + 8 * c);
@@ -957,8 +986,7 @@ k_local_tc(double* Q, double* __restrict__ Iout, float* __restrict__ Pface, floa
       });
       const float (&a)[kNq] = af[s];
       __syncthreads();
-      static_for<0, BT8 / 8>([&](auto cc) {
-        constexpr int c = decltype(cc)::value;
+      for_chunks<BT8 / 8, L::ROLL>([&](int c) {
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = 0.0f;
