@@ -132,3 +132,49 @@ def test_measured_hbm_peak_and_fallback(monkeypatch, tmp_path):
     assert bench.measured_hbm_gbs() == 6781.8
     monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
     assert bench.measured_hbm_gbs() == 6800.0
+
+
+def _digest_tree(root, kernel_text):
+    pkg = root / "paper_1903_11521_gb300"
+    (pkg / "csrc").mkdir(parents=True)
+    (pkg / "_build" / "gen").mkdir(parents=True)
+    (pkg / "csrc" / "ader_kernels.cuh").write_text(kernel_text)
+    (pkg / "csrc" / "fp_convert.cuh").write_text("int f(int x) { return x; }\n")
+    (pkg / "_build" / "gen" / "yt_rows_o5.cuh").write_text("struct R {};\n")
+    for v in ("lf", "nf"):
+        (pkg / "_build" / "gen" / f"ader_o5_f64_{v}.cu").write_text(f"// unit {v}\nint u_{v};\n")
+
+
+def test_kernel_source_digest_ignores_comments_only(monkeypatch, tmp_path):
+    """The ncu traffic figure is quoted only while the kernel sources hash to the captured
+    version: a comment or whitespace edit keeps the digest, a code edit changes it."""
+    base = "__global__ void k(double* q) {\n  q[0] += 1.0;  // one\n}\n"
+    variants = {
+        "base": base,
+        "comment": "/* block\ncomment */\n__global__ void k(double* q) {\n    q[0] += 1.0;  // two\n}\n",
+        "code": "__global__ void k(double* q) {\n  q[0] += 2.0;  // one\n}\n",
+    }
+    digests = {}
+    for name, text in variants.items():
+        root = tmp_path / name
+        _digest_tree(root, text)
+        monkeypatch.setattr(bench, "ROOT", str(root))
+        digests[name] = bench.kernel_source_digest(6, "f64")
+    assert digests["base"] == digests["comment"]
+    assert digests["base"] != digests["code"]
+    # a missing generated unit changes it too (a stale or partial build is not the capture)
+    (tmp_path / "base" / "paper_1903_11521_gb300" / "_build" / "gen" / "ader_o5_f64_nf.cu").unlink()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "base"))
+    assert bench.kernel_source_digest(6, "f64") != digests["base"]
+
+
+def test_ncu_traffic_table_is_per_element_of_a_plausible_size():
+    """Each captured traffic figure is bytes per element of one launch pair, between the
+    algorithmic bytes of the FP64 step (Q, I, face projections, local flux products) and
+    a few times that."""
+    for digest, per_order in bench.NCU_TRAFFIC_PER_ELEMENT.items():
+        assert len(digest) == 16
+        for order, per_element in per_order.items():
+            B = basis.n_basis(order - 1)
+            algorithmic = 9 * B * 8 * 4                # Q read + written, I written + read
+            assert algorithmic <= per_element <= 4 * algorithmic, (digest, order, per_element)
